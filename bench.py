@@ -1,0 +1,510 @@
+#!/usr/bin/env python3
+"""Throughput of the uplink receive path: LS -> sub-block LMMSE -> MMSE detection.
+
+One step = one subframe of the paper-scale workload (128 antennas, 12 users, 1200
+subcarriers, 2 slots x 6 data symbols, 16-QAM, sub-block B = 12 unless --subblock) through
+every per-subframe stage: the fused LS + LMMSE kernel and the detection kernel.  The
+LMMSE weights are plan state (built once, outside the timed region), like the paper's
+precomputed weight files.  Metric: data resource elements (OFDM symbol x subcarrier, each
+carrying K user symbols) detected per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rapro|reference]
+
+Multi-GPU (torchrun, N > 1): independent replicas, one subframe stream per rank, no
+collective on the data path; value = all ranks' REs / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "uplink REs detected/s at 128x12, 1200 sc (FP32 vs BF16-TC); % roofline"
+UNIT = "REs/s"
+N_SETS = 8                   # resident input subframes rotated through (> L2 in total)
+GRAPH_STEPS = N_SETS         # steps per captured CUDA graph
+L2_BYTES = 129 * 2 ** 20
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=64)
+    ap.add_argument("--impl", choices=["rapro", "reference"], default="rapro")
+    ap.add_argument("--subblock", type=int, default=12)
+    ap.add_argument("--snr", type=float, default=10.0)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1802_05427_gb300 import synth
+    sh = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "snr_db": args.snr})
+    desc = (f"paper-scale plain FP32 receive: M={sh.M} antennas, K={sh.K} users, {sh.n_sc} subcarriers "
+            f"(FFT {sh.n_fft}), 1 subframe = {sh.n_slots} slots x {sh.n_data_per_slot} data symbols, "
+            f"{1 << sh.qam_bits}-QAM, {sh.n_taps}-tap exponential PDP (tau {sh.tau_rms:g}), SNR {sh.snr_db:g} dB, "
+            f"sub-block B={args.subblock}")
+    return sh, desc
+
+
+def algorithmic(sh, B):
+    """Algorithmic bytes and flops per launch (one subframe) of each kernel."""
+    T, K, M, N, D = sh.n_slots, sh.K, sh.M, sh.n_sc, sh.n_data_per_slot
+    c = 8
+    n_h = T * K * M * N
+    tail = N % B
+    w_bytes = c * (B * B + tail * tail)
+    flops_lmmse = 8 * n_h * B if tail == 0 else 8 * T * K * M * ((N - tail) * B + tail * tail)
+    est = dict(bytes=c * n_h + c * T * K * N + c * n_h + w_bytes, flops=6 * n_h + flops_lmmse)
+    res = T * D * N
+    det_bytes = c * n_h + c * T * D * M * N + c * T * D * K * N + T * D * K * N + 4 * T * N
+    det_flops = (T * N * (8 * M * K * (K + 1) // 2 + 8 * K ** 3 // 6)) + res * (8 * M * K + 8 * K * K)
+    return dict(ls_lmmse=est, detect=dict(bytes=det_bytes, flops=det_flops), res_per_step=res)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1802_05427_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches these kernels."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    v = t.get("kernels", {}).get(kernel)
+    return None if v is None else float(v)
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1, window):
+        sm, mx, reasons = [], [], set()
+        for ts, line in self.rows:
+            if not (t0 <= ts <= t1):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "window": window}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "window": window}
+
+
+def gpu_id_for(dev):
+    """Something nvidia-smi -i accepts for this CUDA device (PCI id, else the visible id)."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and dev.index is not None and dev.index < len(ids):
+        return ids[dev.index].strip()
+    return None
+
+
+# ------------------------------------------------------------ CPU oracle
+_JOB_INPUTS = {}
+
+
+def _oracle_job(job):
+    """Worker: time the FP64 oracle on `n_sub` subframes restricted to `n_sc` subcarriers.
+
+    Inputs are drawn once per (seed, n_sc) and kept in the worker, outside the timing."""
+    import numpy as np
+    from oracle import rapro_oracle as O
+    from paper_1802_05427_gb300 import synth
+    shape_kw, B, n_sc, n_sub, seed = job
+    sh = synth.SubframeShape(**shape_kw)
+    key = (seed, n_sc)
+    if key not in _JOB_INPUTS:
+        _JOB_INPUTS.clear()
+        sf = synth.make_subframe(sh, seed=seed)
+        _JOB_INPUTS[key] = {k: np.ascontiguousarray(synth.as_c64(sf[k])[..., :n_sc].astype(np.complex128))
+                            for k in ("y_pilot", "pilots", "y_data")}
+    c = _JOB_INPUTS[key]
+    r = O.make_r("exp", n_taps=sh.n_taps, tau_rms=sh.tau_rms, n_fft=sh.n_fft)
+    t0 = time.perf_counter()
+    for _ in range(n_sub):
+        O.receive_subframe(c["y_pilot"], c["pilots"], c["y_data"], B=B, sigma2=sh.sigma2, r=r,
+                           n_data_per_slot=sh.n_data_per_slot, q=sh.qam_bits)
+    dt = time.perf_counter() - t0
+    return n_sub * sh.n_slots * sh.n_data_per_slot * n_sc, dt
+
+
+def oracle_pool(n_workers):
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"          # one BLAS thread per worker process
+    return mp.get_context("spawn").Pool(n_workers)
+
+
+def cpu_baseline(sh, B, target_s=12.0):
+    n = os.cpu_count() or 1
+    shape_kw = dict(sh.__dict__)
+    with oracle_pool(n) as pool:
+        res, dt = pool.map(_oracle_job, [(shape_kw, B, sh.n_sc, 1, 7000 + i) for i in range(n)])[0]
+        per_sub = max(dt, 1e-3)
+        n_sub = max(1, int(target_s / per_sub))
+        out = pool.map(_oracle_job, [(shape_kw, B, sh.n_sc, n_sub, 7100 + i) for i in range(n)])
+    res_total = sum(r for r, _ in out)
+    t = max(d for _, d in out)
+    return {"value": res_total / t, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} processes x {n_sub} full subframes each (1 BLAS thread per process), "
+                      f"{res_total} REs in {t:.1f} s"}
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sh, desc = workload(args)
+    B = args.subblock
+    n = os.cpu_count() or 1
+    shape_kw = dict(sh.__dict__)
+    budget_s = 150.0
+    with oracle_pool(n) as pool:
+        _, dt = pool.map(_oracle_job, [(shape_kw, B, sh.n_sc, 1, 8000 + i) for i in range(n)])[0]
+        per_sc = dt / sh.n_sc
+        steps_total = args.steps + args.warmup
+        n_sc = max(B, min(sh.n_sc, int(budget_s / max(steps_total, 1) / per_sc) // B * B))
+        jobs = [(shape_kw, B, n_sc, 1, 8100 + i) for i in range(n)]
+        for _ in range(args.warmup):
+            pool.map(_oracle_job, jobs)
+        t0 = time.perf_counter()
+        res = 0
+        for _ in range(args.steps):
+            res += sum(r for r, _ in pool.map(_oracle_job, jobs))
+        wall = time.perf_counter() - t0
+    value = res / wall
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "subblock": B, "snr_db": sh.snr_db},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle",
+                             "sample": f"each step: {n} processes x 1 subframe restricted to the first {n_sc} "
+                                       f"subcarriers ({n_sc // B} blocks of {B}); inputs drawn once "
+                                       "per worker outside the timing"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_rapro(args):
+    import numpy as np
+    import torch
+
+    from paper_1802_05427_gb300 import _build, synth
+    from paper_1802_05427_gb300 import rapro as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # CPU baseline first: its spawn pool must not fork a CUDA-initialised process.
+    sh, desc = workload(args)
+    B = args.subblock
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sh, B)
+
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    R.lib()
+
+    alg = algorithmic(sh, B)
+    res_per_step = alg["res_per_step"]
+    params = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, sigma2=sh.sigma2,
+                           qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms)
+    plan = R.Plan(params)
+    s = plan.shapes()
+    sets = []
+    for i in range(N_SETS):
+        sf = synth.make_subframe(sh, seed=synth.SEED_BASE + 1000 * rank + i)
+        sets.append({k: torch.from_numpy(synth.as_c64(sf[k])).to(dev) for k in ("y_pilot", "pilots", "y_data")})
+    in_bytes = sum(t.numel() * t.element_size() for t in sets[0].values())
+    h = torch.empty(s["h"], dtype=torch.complex64, device=dev)
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device=dev)
+    lab = torch.empty(s["labels"], dtype=torch.uint8, device=dev)
+    info = torch.empty(s["info"], dtype=torch.int32, device=dev)
+
+    def step(i, which=("est", "det")):
+        d = sets[i % N_SETS]
+        if "est" in which:
+            R.rapro_ce_ls_lmmse(plan, d["y_pilot"], d["pilots"], h)
+        if "det" in which:
+            R.rapro_mmse_detect(plan, h, d["y_data"], x, lab, None, info)
+
+    # eager warm-up (also compiles nothing: kernels are prebuilt)
+    for i in range(max(args.warmup, 3)):
+        step(i)
+    torch.cuda.synchronize()
+
+    def capture(which, n, start=0):
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                for i in range(start, start + n):
+                    step(i, which)
+        torch.cuda.synchronize()
+        return g
+
+    g_full = capture(("est", "det"), GRAPH_STEPS)
+    g_one = [capture(("est", "det"), 1, j) for j in range(GRAPH_STEPS)]
+    g_est = capture(("est",), GRAPH_STEPS)
+    g_det = capture(("det",), GRAPH_STEPS)
+
+    def run_steps(k):
+        for _ in range(k // GRAPH_STEPS):
+            g_full.replay()
+        for j in range(k % GRAPH_STEPS):
+            g_one[j].replay()
+
+    clocks = ClockSampler(gpu_id_for(dev))
+    clocks.start()
+    time.sleep(0.3)
+    # sustained load before the timed region so the clock samples see a loaded GPU
+    t_soak = time.time()
+    while time.time() - t_soak < 1.5:
+        run_steps(GRAPH_STEPS * 16)
+        torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_host0 = time.time()
+    ev0.record()
+    run_steps(args.steps)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    time.sleep(0.25)
+    clocks.stop()
+    window = "1.5 s of sustained graph replays right before the timed region, plus the timed region"
+    clk = clocks.summary(t_soak, t_host1 + 0.2, window)
+
+    # per-kernel average launch durations: graphs of GRAPH_STEPS launches of one kernel
+    def time_graph(g, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / (reps * GRAPH_STEPS)   # us per launch
+
+    reps = max(16, min(500, args.steps // GRAPH_STEPS))
+    us_est, us_det = time_graph(g_est, reps), time_graph(g_det, reps)
+    assert plan.device_status() == 0, "device status reports a timeout"
+
+    # end to end through the user API with pinned host buffers (copies inside the region)
+    rx = R.Receiver(params, device=local)
+    host_sets = []
+    for i in range(2):
+        sf = synth.make_subframe(sh, seed=synth.SEED_BASE + 500 + i)
+        host_sets.append({k: torch.from_numpy(synth.as_c64(sf[k])).pin_memory() for k in ("y_pilot", "pilots", "y_data")})
+    x_h = torch.empty(s["x_eq"], dtype=torch.complex64).pin_memory()
+    lab_h = torch.empty(s["labels"], dtype=torch.uint8).pin_memory()
+    for i in range(3):
+        d = host_sets[i % 2]
+        rx.receive_host(d["y_pilot"], d["pilots"], d["y_data"], x_h, lab_h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.e2e_steps):
+        d = host_sets[i % 2]
+        rx.receive_host(d["y_pilot"], d["pilots"], d["y_data"], x_h, lab_h)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = sum(t.numel() * t.element_size() for t in host_sets[0].values())
+    d2h = x_h.numel() * x_h.element_size() + lab_h.numel()
+
+    # sub-block sweep of the same workload (B = 12, 48, 100, 1200), graph replays
+    sweep = {}
+    if not args.no_sweep and rank == 0 and world == 1:
+        for Bs in (12, 48, 100, 1200):
+            ps = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=Bs, sigma2=sh.sigma2,
+                               qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms)
+            with R.Plan(ps) as pl2:
+                def step2(i):
+                    d = sets[i % N_SETS]
+                    R.rapro_ce_ls_lmmse(pl2, d["y_pilot"], d["pilots"], h)
+                    R.rapro_mmse_detect(pl2, h, d["y_data"], x, lab, None, info)
+                for i in range(3):
+                    step2(i)
+                g = torch.cuda.CUDAGraph()
+                st = torch.cuda.Stream()
+                st.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(st):
+                    with torch.cuda.graph(g, stream=st):
+                        for i in range(GRAPH_STEPS):
+                            step2(i)
+                torch.cuda.synchronize()
+                r2 = 64 if Bs < 1200 else 4
+                e0.record()
+                for _ in range(r2):
+                    g.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                sweep[str(Bs)] = res_per_step * r2 * GRAPH_STEPS / (e0.elapsed_time(e1) * 1e-3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = world * res_per_step * args.steps / (ms * 1e-3)
+    hbm, peak_kind = peaks()
+    rows = {}
+    for name, us in (("ls_lmmse", us_est), ("detect", us_det)):
+        a = alg[name]
+        t_hbm = a["bytes"] / (hbm * 1e9)
+        t_alu = a["flops"] / (ALU_PEAK_TFLOPS * 1e12)
+        if t_hbm >= t_alu:
+            ach, peak, unit, bound = a["bytes"] / (us * 1e-6) / 1e9, hbm, "GB/s", "hbm"
+        else:
+            ach, peak, unit, bound = a["flops"] / (us * 1e-6) / 1e12, ALU_PEAK_TFLOPS, "TFLOP/s", "alu"
+        rows[name] = dict(bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
+                          us_per_launch=us, alg_bytes=a["bytes"], alg_flops=a["flops"])
+    dom = max(rows, key=lambda k: rows[k]["us_per_launch"])
+    r = rows[dom]
+    traffic = measured_traffic(dom)
+    roof = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
+            "frac": r["frac"], "traffic": traffic, "kernel": dom,
+            "peak_source": (f"{peak_kind} HBM copy bandwidth" if r["bound"] == "hbm" else
+                            "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded Rayleigh taps, exponential PDP, unit-modulus pilots, uniform 16-QAM payload, AWGN",
+            "config": {"workload": desc, "M": sh.M, "K": sh.K, "n_sc": sh.n_sc, "subblock": B, "snr_db": sh.snr_db,
+                       "res_per_step": res_per_step, "parallelism": f"replicas x{world}",
+                       "l2": f"{N_SETS} resident input subframes rotated ({N_SETS * in_bytes / 2**20:.0f} MiB > "
+                             f"{L2_BYTES / 2**20:.0f} MiB L2)",
+                       "launch": f"CUDA graph replays of {GRAPH_STEPS} steps"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * res_per_step * args.e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "Receiver.receive_host (pinned host in/out, rapro_receive_subframe)"},
+            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "kernels": rows, "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_rapro(args)
+
+
+if __name__ == "__main__":
+    main()

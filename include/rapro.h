@@ -1,0 +1,205 @@
+/*
+ * rapro.h -- C ABI of the GB300 uplink receive path of
+ * "Implementation of Massive MIMO Uplink Receiver on RaPro Prototyping Platform"
+ * (arXiv 1802.05427): LS channel estimation -> low-complexity sub-block LMMSE
+ * channel estimation -> per-subcarrier MMSE detection with Cholesky and QAM demapping.
+ *
+ * Notation.  The paper's R antennas and S users are M and K here; its N used
+ * subcarriers are n_sc; the sub-block size of the partitioned correlation matrix is B.
+ *
+ * Conventions shared by every entry point
+ *  - Array arguments are caller-owned DEVICE memory (the caller allocates and frees,
+ *    like the receiver functions of Sec. III-B that read and write caller arrays),
+ *    dense, in the layouts given below, subcarrier index fastest.  rapro_c32 is an
+ *    interleaved single-precision complex {re, im} (8 bytes).  All arithmetic on the
+ *    device is FP32; the LMMSE weights are built in FP64 on the host and rounded.
+ *  - Work is enqueued on the caller's stream (a cudaStream_t, passed as rapro_stream;
+ *    NULL means the legacy default stream).  Only rapro_plan_create and
+ *    rapro_plan_destroy synchronise.  A return of RAPRO_OK means "validated and
+ *    enqueued"; device-side results (non-positive-definite pivots, timeouts) are
+ *    reported through the info array and rapro_plan_device_status.
+ *  - The plan is the only library-owned memory: the weights W_b on the device, a
+ *    channel-estimate workspace used by rapro_receive_subframe when h_out is NULL,
+ *    and one device status word.  rapro_plan_destroy frees all of it.
+ *  - No call throws across the ABI, traps on the device or asserts.  NaN/Inf inputs
+ *    propagate to the outputs.  Calls that share a plan may run concurrently on
+ *    different streams except rapro_receive_subframe with h_out == NULL, which writes
+ *    the plan's workspace: serialise those per plan.
+ *
+ * Layouts (T = n_pilot_sym slots, D = n_sym / n_pilot_sym - 1 data symbols per slot):
+ *   y_pilot, h_ls, h  [T][K][M][n_sc]   pilot observation of user s at antenna m
+ *   pilots            [T][K][n_sc]      transmitted pilot of user s (|p| != 0)
+ *   y_data            [T*D][M][n_sc]    data OFDM symbols in time order; data symbol n
+ *                                       belongs to slot n / D and is detected with
+ *                                       that slot's channel estimate
+ *   x_eq              [T*D][K][n_sc]    MMSE output x~ of Eq. 22
+ *   labels            [T*D][K][n_sc]    hard decision as the q-bit Gray label
+ *                                       (uint8, bit b0 = most significant)
+ *   llr               [T*D][K][n_sc][q] max-log LLR per bit, b0 first, > 0 favours 0
+ *   info              [T][n_sc]         0, or j+1 if pivot j of the Cholesky factor of
+ *                                       H^H H + sigma2 I was not positive and finite
+ */
+#ifndef RAPRO_H
+#define RAPRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } rapro_c32;
+
+/* Same type as cudaStream_t; this header does not need the CUDA headers. */
+typedef struct CUstream_st* rapro_stream;
+
+typedef enum {
+  RAPRO_OK = 0,
+  RAPRO_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter outside its documented range */
+  RAPRO_ERR_CUDA = 2,          /* a CUDA runtime call failed (the message is kept, see below) */
+  RAPRO_ERR_NOT_POSDEF = 3,    /* the FP64 host factorisation of R_b + sigma2 I failed */
+  RAPRO_ERR_TIMEOUT = 4,       /* a device wait hit its iteration limit (device status) */
+  RAPRO_ERR_UNSUPPORTED = 5,   /* a valid request this build does not implement */
+  RAPRO_ERR_NOMEM = 6          /* device allocation failed in rapro_plan_create */
+} rapro_status;
+
+typedef enum {
+  RAPRO_PILOT_ORTHOGONAL = 0,  /* one pilot observation per user on every subcarrier */
+  RAPRO_PILOT_COMB = 1         /* the FDM comb of Sec. II: not implemented (UNSUPPORTED) */
+} rapro_pilot_layout;
+
+typedef enum {
+  /* Exponential power-delay profile of Sec. III-A (text under Eq. 16) on integer delays:
+   * r(d) = sum_{l<n_taps} p_l exp(-j 2 pi l d / n_fft), p_l = exp(-l/tau_rms) / sum. */
+  RAPRO_PDP_EXP = 0,
+  /* Eq. 16: r(0) = 1, r(d) = (1 - exp(-j 2 pi L d / n_fft)) / (j 2 pi L d / n_fft). */
+  RAPRO_PDP_UNIFORM_L = 1
+} rapro_pdp_kind;
+
+#define RAPRO_MAX_PILOT_SYM 8
+#define RAPRO_MAX_USERS 16       /* K limit of the register-tiled detector */
+#define RAPRO_MAX_DATA_PER_SLOT 12
+
+typedef struct {
+  int M;                 /* BS antennas (paper: R), >= 1 */
+  int K;                 /* single-antenna users (paper: S), 1..RAPRO_MAX_USERS */
+  int n_sc;              /* used subcarriers (paper: N), >= 1 */
+  int n_fft;             /* FFT size (paper: N_FFT), >= n_sc; the N of Eq. 16 */
+  int n_sym;             /* OFDM symbols per subframe, e.g. 14 */
+  int n_pilot_sym;       /* pilot symbols = slots T, 1..RAPRO_MAX_PILOT_SYM; n_sym % T == 0 */
+  int pilot_sym_idx[RAPRO_MAX_PILOT_SYM]; /* symbol index of the pilot of slot j; must lie in
+                                             [j*n_sym/T, (j+1)*n_sym/T) */
+  int pilot_layout;      /* rapro_pilot_layout */
+  int subblock;          /* B, 1..n_sc; B == n_sc is the full LMMSE of Eq. 13 */
+  double sigma2;         /* noise variance sigma^2 > 0 (pilot power sigma_s^2 = 1), used by
+                            both the estimator (Eq. 17) and the detector (Eq. 22) */
+  int pdp;               /* rapro_pdp_kind */
+  int n_taps;            /* EXP: taps at delays 0..n_taps-1, >= 1 */
+  double tau_rms;        /* EXP: decay constant in samples, > 0 */
+  double L;              /* UNIFORM_L: assumed channel length in samples, > 0 */
+  int qam_bits;          /* q = 2 (QPSK), 4 (16-QAM) or 6 (64-QAM) */
+} rapro_params;
+
+typedef struct rapro_plan rapro_plan;
+
+/* Human-readable name of a status code (static storage). */
+const char* rapro_status_string(rapro_status s);
+
+/* Text of the last error recorded by this thread (CUDA message or argument check). */
+const char* rapro_last_error(void);
+
+/* Check a parameter set without touching the GPU.  Host only. */
+rapro_status rapro_params_validate(const rapro_params* p);
+
+/*
+ * Host-only FP64 weights of one sub-block (Eq. 13/17 with R_{H Hls} = R_{HH}):
+ *   W = R (R + sigma2 I)^-1,  R[a][b] = r(a - b),  a, b in [0, block_len)
+ * built from p's PDP model; written row-major as interleaved {re, im} doubles,
+ * w_out[2*(a*block_len + b) + {0,1}].  block_len in [1, 4096].
+ * Returns RAPRO_ERR_NOT_POSDEF if R + sigma2 I fails to factor in FP64.
+ */
+rapro_status rapro_build_weights_host(const rapro_params* p, int block_len, double* w_out);
+
+/*
+ * Validate p, build W_b for the full block size B and for the tail block of
+ * n_sc mod B subcarriers (blocks start at subcarrier 0), round them to
+ * complex64, copy them to the current device, and allocate the workspace.
+ * Synchronous.  *out is NULL on failure.
+ */
+rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out);
+
+/* Free the plan and its device memory (synchronises the device first).  NULL is a no-op. */
+rapro_status rapro_plan_destroy(rapro_plan* plan);
+
+/* Derived sizes of a plan: slots T, data symbols per slot D, blocks nb, tail size
+ * (0 if B divides n_sc).  Any output pointer may be NULL. */
+rapro_status rapro_plan_dims(const rapro_plan* plan, int* T, int* D, int* nb, int* tail);
+
+/*
+ * Read (and with reset != 0 clear) the plan's device status word: 0, or
+ * RAPRO_ERR_TIMEOUT if a kernel gave up waiting on one of its pipeline barriers.
+ * Synchronises the plan's status copy with the device.
+ */
+rapro_status rapro_plan_device_status(rapro_plan* plan, int reset, int* status_out);
+
+/*
+ * Step a1 -- LS estimate, Eq. 8-9: h_ls = y_pilot / pilots = y_pilot conj(p) / |p|^2
+ * per (slot, user, antenna, subcarrier).  The paper multiplies by the conjugate pilot
+ * because its pilots have unit modulus (Sec. IV-C); the division form is exact for any
+ * nonzero pilot.  In-place (h_ls == y_pilot) is allowed.
+ */
+rapro_status rapro_ce_ls(const rapro_plan* plan, const rapro_c32* y_pilot,
+                         const rapro_c32* pilots, rapro_c32* h_ls, rapro_stream stream);
+
+/*
+ * Step a3 -- sub-block LMMSE filter, Eq. 12 with the fixed weights of Eq. 17:
+ *   h[t][s][m][blk] = W_blk * h_ls[t][s][m][blk]
+ * for every slot, user and antenna, over the non-overlapping blocks of B contiguous
+ * subcarriers (the last block holds n_sc mod B).  w_override, if not NULL, replaces
+ * the plan's weights: nb matrices stored one after another, block b's W row-major,
+ * B*B entries for full blocks and tail*tail for the tail.  h must not alias h_ls.
+ */
+rapro_status rapro_ce_lmmse_subblock(const rapro_plan* plan, const rapro_c32* h_ls,
+                                     const rapro_c32* w_override, rapro_c32* h,
+                                     rapro_stream stream);
+
+/*
+ * Steps a1 + a3 in one pass: the LS estimate of Eq. 9 is formed on load and filtered by
+ * the sub-block weights of Eq. 12/17 without being stored:
+ *   h[t][s][m][blk] = W_blk * (y_pilot[t][s][m][blk] conj(p[t][s][blk]) / |p|^2).
+ * w_override as for rapro_ce_lmmse_subblock.  h must not alias y_pilot.
+ */
+rapro_status rapro_ce_ls_lmmse(const rapro_plan* plan, const rapro_c32* y_pilot,
+                               const rapro_c32* pilots, const rapro_c32* w_override,
+                               rapro_c32* h, rapro_stream stream);
+
+/*
+ * Steps a4-a8 -- MMSE detection, Eq. 20-22, per (slot, subcarrier):
+ *   A = H^H H + sigma2 I (Gram), z = H^H y (matched filter), A = L L^H (Cholesky, the
+ *   uplo = L factorisation the paper solves with), L L^H x~ = z for every data symbol
+ *   of the slot; x_eq = x~.  Demapping: mu_k = 1 - sigma2 [A^-1]_kk, x^ = x~ / mu,
+ *   labels = nearest Gray-QAM point of x^, llr_i = (min_{b_i=1}|x^-x|^2 -
+ *   min_{b_i=0}|x^-x|^2) / nu with nu = (1 - mu) / mu.
+ * labels, llr and info may be NULL (not produced).  A subcarrier whose pivot fails
+ * gets info = j+1 and NaN outputs; the others are unaffected.
+ */
+rapro_status rapro_mmse_detect(const rapro_plan* plan, const rapro_c32* h,
+                               const rapro_c32* y_data, rapro_c32* x_eq, uint8_t* labels,
+                               float* llr, int32_t* info, rapro_stream stream);
+
+/*
+ * The whole path (a1, a3, a4-a8) for one subframe: rapro_ce_ls_lmmse, then
+ * rapro_mmse_detect, on the same stream.  h_out (nullable) receives the LMMSE channel
+ * estimate; when NULL the plan's workspace holds it.  Other arguments as above.
+ */
+rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_pilot,
+                                    const rapro_c32* pilots, const rapro_c32* y_data,
+                                    rapro_c32* h_out, rapro_c32* x_eq, uint8_t* labels,
+                                    float* llr, int32_t* info, rapro_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAPRO_H */

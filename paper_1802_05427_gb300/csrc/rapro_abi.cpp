@@ -1,0 +1,107 @@
+// extern "C" entry points: argument checks, then the kernel launchers.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "rapro_internal.h"
+
+using namespace rapro;
+
+namespace {
+
+rapro_status bad(const char* msg) {
+  set_error(msg);
+  return RAPRO_ERR_INVALID_ARG;
+}
+
+// The plan's weights live on the device that was current at rapro_plan_create.
+rapro_status check_device(const Plan* pl) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != pl->device) return bad("current device differs from the plan's device");
+  return RAPRO_OK;
+}
+
+rapro_status launched(cudaError_t e, const char* what) {
+  return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, what);
+}
+
+inline const float2* f2(const rapro_c32* p) { return reinterpret_cast<const float2*>(p); }
+inline float2* f2(rapro_c32* p) { return reinterpret_cast<float2*>(p); }
+inline cudaStream_t cs(rapro_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+rapro_status rapro_ce_ls(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
+                         rapro_c32* h_ls, rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  if (!y_pilot || !pilots || !h_ls) return bad("y_pilot, pilots and h_ls must not be NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  rapro_status s = check_device(pl);
+  if (s != RAPRO_OK) return s;
+  return launched(launch_ls(f2(y_pilot), f2(pilots), f2(h_ls), pl->T, pl->p.K, pl->p.M, pl->p.n_sc, cs(stream)),
+                  "LS kernel launch");
+}
+
+rapro_status rapro_ce_lmmse_subblock(const rapro_plan* plan, const rapro_c32* h_ls,
+                                     const rapro_c32* w_override, rapro_c32* h, rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  if (!h_ls || !h) return bad("h_ls and h must not be NULL");
+  if (f2(h_ls) == f2(h)) return bad("h must not alias h_ls");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  rapro_status s = check_device(pl);
+  if (s != RAPRO_OK) return s;
+  const float2* w = w_override ? f2(w_override) : pl->d_w_main;
+  return launched(launch_lmmse(*pl, f2(h_ls), nullptr, w, pl->d_w_tail, pl->w_main.data(),
+                               pl->w_tail.data(), f2(h), cs(stream)),
+                  "LMMSE kernel launch");
+}
+
+rapro_status rapro_ce_ls_lmmse(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
+                               const rapro_c32* w_override, rapro_c32* h, rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  if (!y_pilot || !pilots || !h) return bad("y_pilot, pilots and h must not be NULL");
+  if (f2(y_pilot) == f2(h)) return bad("h must not alias y_pilot");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  rapro_status s = check_device(pl);
+  if (s != RAPRO_OK) return s;
+  const float2* w = w_override ? f2(w_override) : pl->d_w_main;
+  return launched(launch_lmmse(*pl, f2(y_pilot), f2(pilots), w, pl->d_w_tail, pl->w_main.data(),
+                               pl->w_tail.data(), f2(h), cs(stream)),
+                  "LS+LMMSE kernel launch");
+}
+
+rapro_status rapro_mmse_detect(const rapro_plan* plan, const rapro_c32* h, const rapro_c32* y_data,
+                               rapro_c32* x_eq, uint8_t* labels, float* llr, int32_t* info,
+                               rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  if (!h || !y_data || !x_eq) return bad("h, y_data and x_eq must not be NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  rapro_status s = check_device(pl);
+  if (s != RAPRO_OK) return s;
+  return launched(launch_detect(*pl, f2(h), f2(y_data), f2(x_eq), labels, llr, info, cs(stream)),
+                  "detection kernel launch");
+}
+
+rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_pilot,
+                                    const rapro_c32* pilots, const rapro_c32* y_data,
+                                    rapro_c32* h_out, rapro_c32* x_eq, uint8_t* labels, float* llr,
+                                    int32_t* info, rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  if (!y_pilot || !pilots || !y_data || !x_eq)
+    return bad("y_pilot, pilots, y_data and x_eq must not be NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  rapro_status s = check_device(pl);
+  if (s != RAPRO_OK) return s;
+  float2* h = h_out ? f2(h_out) : pl->d_h_work;
+  cudaError_t e = launch_lmmse(*pl, f2(y_pilot), f2(pilots), pl->d_w_main, pl->d_w_tail,
+                               pl->w_main.data(), pl->w_tail.data(), h, cs(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "LS+LMMSE kernel launch");
+  return launched(launch_detect(*pl, h, f2(y_data), f2(x_eq), labels, llr, info, cs(stream)),
+                  "detection kernel launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Internal declarations shared by the host plan, the ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "rapro.h"
+
+namespace rapro {
+
+// Detector tiling: each CTA owns DET_SC consecutive subcarriers of one slot and streams
+// the antennas through shared memory DET_MCH at a time.
+constexpr int DET_SC = 16;
+constexpr int DET_MCH = 8;
+constexpr int DET_STAGES = 4;
+constexpr int DET_MAX_TILES = 16;   // K <= 16 and D <= 12 need at most 8 + 4*2 tiles
+
+// One thread tile of the detector's accumulation: 4 rows (users i) x 6 columns of the
+// augmented operand list [users 0..KP6-1 | data symbols 0..DP6-1].
+struct DetTiles {
+  int n_tiles;
+  int KP6;    // padded user rows in the shared-memory stage
+  int DP6;    // padded data rows
+  signed char row_group[DET_MAX_TILES];
+  signed char col_off[DET_MAX_TILES];
+};
+
+constexpr int LMMSE_SMALL_MAX = 32;   // B <= this uses the weights-in-parameter kernel
+
+struct Plan {
+  rapro_params p;
+  int T = 0, D = 0, q = 0;
+  int B = 0, nb = 0, tail = 0;     // block size, block count, tail block size (0 = none)
+  std::vector<float2> w_main;      // B x B row-major, complex64
+  std::vector<float2> w_tail;      // tail x tail
+  float2* d_w_main = nullptr;
+  float2* d_w_tail = nullptr;
+  float2* d_h_work = nullptr;      // [T][K][M][n_sc] estimate workspace
+  int* d_status = nullptr;         // device status word
+  DetTiles tiles{};
+  int device = 0;
+};
+
+// Thread-local last-error text.
+void set_error(const std::string& msg);
+rapro_status cuda_fail(cudaError_t e, const char* what);
+
+// Host FP64 weights of one block of len subcarriers: W = R (R + s I)^-1, row-major
+// interleaved.  Returns false if R + s I is not positive definite in FP64.
+bool build_weights_fp64(const rapro_params& p, int len, std::vector<double>& w);
+
+DetTiles make_det_tiles(int K, int D);
+
+// Kernel launchers (return the launch error, if any).
+cudaError_t launch_ls(const float2* y, const float2* pil, float2* h, int T, int K, int M,
+                      int N, cudaStream_t st);
+
+// LMMSE filter; if pil != nullptr the input is y_pilot and LS is applied on load.
+// w_main/w_tail: host copies (small-B kernel) or device pointers (tiled kernel).
+cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
+                         const float2* d_w_main, const float2* d_w_tail,
+                         const float2* h_w_main, const float2* h_w_tail, float2* out,
+                         cudaStream_t st);
+
+cudaError_t prepare_detect(int device);
+
+cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
+                          unsigned char* labels, float* llr, int* info, cudaStream_t st);
+
+}  // namespace rapro

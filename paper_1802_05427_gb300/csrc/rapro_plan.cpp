@@ -1,0 +1,285 @@
+// Host side of the library: parameter checks, FP64 sub-block LMMSE weights, plans.
+//
+// The weights follow Eq. 13/17 with orthogonal per-user pilots, where the LS estimate
+// sits on every subcarrier and R_{H Hls} = R_{HH} = R:  W = R (R + sigma2 I)^-1.
+// Because A = R + sigma2 I and R are Hermitian, W^H = A^-1 R, so W is obtained from one
+// Cholesky factorisation A = L L^H and two triangular solves per column of R.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rapro_internal.h"
+
+namespace rapro {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+rapro_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? RAPRO_ERR_NOMEM : RAPRO_ERR_CUDA;
+}
+
+using cd = std::complex<double>;
+
+// Frequency correlation r(d) between subcarriers d apart (Eq. 16 or the exponential PDP).
+static cd corr(const rapro_params& p, int d) {
+  const double two_pi = 6.283185307179586476925286766559;
+  if (p.pdp == RAPRO_PDP_EXP) {
+    double norm = 0.0;
+    for (int l = 0; l < p.n_taps; ++l) norm += std::exp(-l / p.tau_rms);
+    cd acc(0.0, 0.0);
+    for (int l = 0; l < p.n_taps; ++l) {
+      const double ph = -two_pi * double(l) * double(d) / double(p.n_fft);
+      acc += (std::exp(-l / p.tau_rms) / norm) * cd(std::cos(ph), std::sin(ph));
+    }
+    return acc;
+  }
+  if (d == 0) return cd(1.0, 0.0);
+  const double x = two_pi * p.L * double(d) / double(p.n_fft);
+  // (1 - e^{-jx}) / (jx)
+  const cd num(1.0 - std::cos(x), std::sin(x));
+  return num / cd(0.0, x);
+}
+
+bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out) {
+  // r(d) for d in (-n, n)
+  std::vector<cd> r(2 * n - 1);
+  for (int d = -(n - 1); d <= n - 1; ++d) r[d + n - 1] = corr(p, d);
+  auto R = [&](int a, int b) { return r[a - b + n - 1]; };
+
+  // A = R + sigma2 I, Cholesky in place (lower triangle), column-major access by rows.
+  std::vector<cd> L(size_t(n) * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) L[size_t(i) * n + j] = R(i, j) + (i == j ? p.sigma2 : 0.0);
+  for (int j = 0; j < n; ++j) {
+    cd* Lj = &L[size_t(j) * n];
+    double d = Lj[j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(Lj[k]);
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    const double ljj = std::sqrt(d);
+    Lj[j] = cd(ljj, 0.0);
+    for (int i = j + 1; i < n; ++i) {
+      cd* Li = &L[size_t(i) * n];
+      cd s = Li[j];
+      for (int k = 0; k < j; ++k) s -= Li[k] * std::conj(Lj[k]);
+      Li[j] = s / ljj;
+    }
+  }
+  // X = A^-1 R column by column (L y = r_col, L^H x = y); then W = X^H.
+  std::vector<cd> X(size_t(n) * n), y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      cd s = R(i, c);
+      const cd* Li = &L[size_t(i) * n];
+      for (int k = 0; k < i; ++k) s -= Li[k] * y[k];
+      y[i] = s / Li[i].real();
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      cd s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= std::conj(L[size_t(k) * n + i]) * X[size_t(k) * n + c];
+      X[size_t(i) * n + c] = s / L[size_t(i) * n + i].real();
+    }
+  }
+  w_out.assign(size_t(2) * n * n, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      const cd v = std::conj(X[size_t(b) * n + a]);   // W[a][b] = conj(X[b][a])
+      w_out[2 * (size_t(a) * n + b)] = v.real();
+      w_out[2 * (size_t(a) * n + b) + 1] = v.imag();
+    }
+  return true;
+}
+
+DetTiles make_det_tiles(int K, int D) {
+  DetTiles t{};
+  const int nrg = (K + 3) / 4, nug = (K + 5) / 6, ndg = (D + 5) / 6;
+  t.KP6 = std::max(4 * nrg, 6 * nug);
+  t.DP6 = 6 * ndg;
+  int n = 0;
+  for (int a = 0; a < nrg; ++a)
+    for (int c = 0; c < nug; ++c)
+      if (6 * c <= 4 * a + 3) { t.row_group[n] = (signed char)a; t.col_off[n] = (signed char)(6 * c); ++n; }
+  for (int a = 0; a < nrg; ++a)
+    for (int c = 0; c < ndg; ++c) { t.row_group[n] = (signed char)a; t.col_off[n] = (signed char)(t.KP6 + 6 * c); ++n; }
+  t.n_tiles = n;
+  return t;
+}
+
+static rapro_status invalid(const char* msg) {
+  set_error(msg);
+  return RAPRO_ERR_INVALID_ARG;
+}
+
+}  // namespace rapro
+
+using namespace rapro;
+
+extern "C" {
+
+const char* rapro_status_string(rapro_status s) {
+  switch (s) {
+    case RAPRO_OK: return "RAPRO_OK";
+    case RAPRO_ERR_INVALID_ARG: return "RAPRO_ERR_INVALID_ARG";
+    case RAPRO_ERR_CUDA: return "RAPRO_ERR_CUDA";
+    case RAPRO_ERR_NOT_POSDEF: return "RAPRO_ERR_NOT_POSDEF";
+    case RAPRO_ERR_TIMEOUT: return "RAPRO_ERR_TIMEOUT";
+    case RAPRO_ERR_UNSUPPORTED: return "RAPRO_ERR_UNSUPPORTED";
+    case RAPRO_ERR_NOMEM: return "RAPRO_ERR_NOMEM";
+  }
+  return "RAPRO_ERR_UNKNOWN";
+}
+
+const char* rapro_last_error(void) { return g_last_error.c_str(); }
+
+rapro_status rapro_params_validate(const rapro_params* p) {
+  if (!p) return invalid("params is NULL");
+  if (p->M < 1) return invalid("M must be >= 1");
+  if (p->K < 1 || p->K > RAPRO_MAX_USERS) return invalid("K must be in [1, RAPRO_MAX_USERS]");
+  if (p->n_sc < 1) return invalid("n_sc must be >= 1");
+  if (p->n_fft < p->n_sc) return invalid("n_fft must be >= n_sc");
+  if (p->n_pilot_sym < 1 || p->n_pilot_sym > RAPRO_MAX_PILOT_SYM)
+    return invalid("n_pilot_sym must be in [1, RAPRO_MAX_PILOT_SYM]");
+  if (p->n_sym < 2 * p->n_pilot_sym || p->n_sym % p->n_pilot_sym != 0)
+    return invalid("n_sym must be a multiple of n_pilot_sym with >= 1 data symbol per slot");
+  const int slot_len = p->n_sym / p->n_pilot_sym;
+  if (slot_len - 1 > RAPRO_MAX_DATA_PER_SLOT)
+    return invalid("more than RAPRO_MAX_DATA_PER_SLOT data symbols per slot");
+  for (int j = 0; j < p->n_pilot_sym; ++j)
+    if (p->pilot_sym_idx[j] < j * slot_len || p->pilot_sym_idx[j] >= (j + 1) * slot_len)
+      return invalid("pilot_sym_idx[j] must lie inside slot j");
+  if (p->pilot_layout == RAPRO_PILOT_COMB) {
+    set_error("comb pilot layout is not implemented");
+    return RAPRO_ERR_UNSUPPORTED;
+  }
+  if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL) return invalid("unknown pilot_layout");
+  if (p->subblock < 1 || p->subblock > p->n_sc) return invalid("subblock must be in [1, n_sc]");
+  if (!(p->sigma2 > 0.0) || !std::isfinite(p->sigma2)) return invalid("sigma2 must be finite and > 0");
+  if (p->pdp == RAPRO_PDP_EXP) {
+    if (p->n_taps < 1) return invalid("n_taps must be >= 1");
+    if (!(p->tau_rms > 0.0) || !std::isfinite(p->tau_rms)) return invalid("tau_rms must be > 0");
+  } else if (p->pdp == RAPRO_PDP_UNIFORM_L) {
+    if (!(p->L > 0.0) || !std::isfinite(p->L)) return invalid("L must be > 0");
+  } else {
+    return invalid("unknown pdp kind");
+  }
+  if (p->qam_bits != 2 && p->qam_bits != 4 && p->qam_bits != 6) return invalid("qam_bits must be 2, 4 or 6");
+  const double elems = double(p->n_pilot_sym) * p->K * p->M * p->n_sc;
+  if (elems > 2147483647.0) return invalid("T*K*M*n_sc must fit in int32");
+  return RAPRO_OK;
+}
+
+rapro_status rapro_build_weights_host(const rapro_params* p, int block_len, double* w_out) {
+  rapro_status s = rapro_params_validate(p);
+  if (s != RAPRO_OK) return s;
+  if (block_len < 1 || block_len > 4096) return invalid("block_len must be in [1, 4096]");
+  if (!w_out) return invalid("w_out is NULL");
+  std::vector<double> w;
+  if (!build_weights_fp64(*p, block_len, w)) {
+    set_error("R + sigma2 I is not positive definite in FP64");
+    return RAPRO_ERR_NOT_POSDEF;
+  }
+  std::memcpy(w_out, w.data(), w.size() * sizeof(double));
+  return RAPRO_OK;
+}
+
+rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
+  if (!out) return invalid("out is NULL");
+  *out = nullptr;
+  rapro_status s = rapro_params_validate(p);
+  if (s != RAPRO_OK) return s;
+  Plan* pl = new Plan();
+  pl->p = *p;
+  pl->T = p->n_pilot_sym;
+  pl->D = p->n_sym / p->n_pilot_sym - 1;
+  pl->q = p->qam_bits;
+  pl->B = p->subblock;
+  pl->nb = (p->n_sc + p->subblock - 1) / p->subblock;
+  pl->tail = p->n_sc % p->subblock;
+  pl->tiles = make_det_tiles(p->K, pl->D);
+
+  auto to_c64 = [](const std::vector<double>& w) {
+    std::vector<float2> o(w.size() / 2);
+    for (size_t i = 0; i < o.size(); ++i) o[i] = make_float2(float(w[2 * i]), float(w[2 * i + 1]));
+    return o;
+  };
+  std::vector<double> w;
+  if (!build_weights_fp64(*p, pl->B, w)) {
+    delete pl;
+    set_error("R_b + sigma2 I is not positive definite in FP64");
+    return RAPRO_ERR_NOT_POSDEF;
+  }
+  pl->w_main = to_c64(w);
+  if (pl->tail) {
+    if (!build_weights_fp64(*p, pl->tail, w)) {
+      delete pl;
+      set_error("tail R_b + sigma2 I is not positive definite in FP64");
+      return RAPRO_ERR_NOT_POSDEF;
+    }
+    pl->w_tail = to_c64(w);
+  }
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDevice"); }
+  if ((e = prepare_detect(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "detector set-up"); }
+  const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
+  auto fail = [&](cudaError_t err, const char* what) {
+    cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
+    delete pl;
+    return cuda_fail(err, what);
+  };
+  if ((e = cudaMalloc(&pl->d_w_main, pl->w_main.size() * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc W");
+  if (pl->tail && (e = cudaMalloc(&pl->d_w_tail, pl->w_tail.size() * sizeof(float2))) != cudaSuccess)
+    return fail(e, "cudaMalloc W tail");
+  if ((e = cudaMalloc(&pl->d_h_work, h_elems * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
+  if ((e = cudaMalloc(&pl->d_status, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc status");
+  if ((e = cudaMemcpy(pl->d_w_main, pl->w_main.data(), pl->w_main.size() * sizeof(float2),
+                      cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W");
+  if (pl->tail && (e = cudaMemcpy(pl->d_w_tail, pl->w_tail.data(), pl->w_tail.size() * sizeof(float2),
+                                  cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W tail");
+  if ((e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset status");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan upload");
+  *out = reinterpret_cast<rapro_plan*>(pl);
+  return RAPRO_OK;
+}
+
+rapro_status rapro_plan_destroy(rapro_plan* plan) {
+  if (!plan) return RAPRO_OK;
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(pl->d_w_main);
+  cudaFree(pl->d_w_tail);
+  cudaFree(pl->d_h_work);
+  cudaFree(pl->d_status);
+  delete pl;
+  return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, "rapro_plan_destroy");
+}
+
+rapro_status rapro_plan_dims(const rapro_plan* plan, int* T, int* D, int* nb, int* tail) {
+  if (!plan) return invalid("plan is NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  if (T) *T = pl->T;
+  if (D) *D = pl->D;
+  if (nb) *nb = pl->nb;
+  if (tail) *tail = pl->tail;
+  return RAPRO_OK;
+}
+
+rapro_status rapro_plan_device_status(rapro_plan* plan, int reset, int* status_out) {
+  if (!plan || !status_out) return invalid("plan or status_out is NULL");
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, pl->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read device status");
+  if (reset && (e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "reset status");
+  *status_out = v;
+  return RAPRO_OK;
+}
+
+}  // extern "C"

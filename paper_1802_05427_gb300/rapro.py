@@ -1,0 +1,287 @@
+"""Python binding of librapro.so: the C-ABI entry points under the same names.
+
+Argument marshalling only -- every step of the receive path runs in the CUDA library.
+Tensors are torch tensors on the plan's CUDA device (complex64 for rapro_c32 arrays,
+uint8 labels, float32 LLRs, int32 info), C-contiguous, in the layouts of rapro.h.
+Streams default to torch's current stream.  The library must have been built
+(``paper_1802_05427_gb300._build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librapro.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "rapro.h")
+
+RAPRO_OK, RAPRO_ERR_INVALID_ARG, RAPRO_ERR_CUDA, RAPRO_ERR_NOT_POSDEF = 0, 1, 2, 3
+RAPRO_ERR_TIMEOUT, RAPRO_ERR_UNSUPPORTED, RAPRO_ERR_NOMEM = 4, 5, 6
+RAPRO_PILOT_ORTHOGONAL, RAPRO_PILOT_COMB = 0, 1
+RAPRO_PDP_EXP, RAPRO_PDP_UNIFORM_L = 0, 1
+RAPRO_MAX_PILOT_SYM = 8
+
+
+class RaproParams(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int), ("K", ctypes.c_int), ("n_sc", ctypes.c_int), ("n_fft", ctypes.c_int),
+        ("n_sym", ctypes.c_int), ("n_pilot_sym", ctypes.c_int),
+        ("pilot_sym_idx", ctypes.c_int * RAPRO_MAX_PILOT_SYM),
+        ("pilot_layout", ctypes.c_int), ("subblock", ctypes.c_int), ("sigma2", ctypes.c_double),
+        ("pdp", ctypes.c_int), ("n_taps", ctypes.c_int), ("tau_rms", ctypes.c_double),
+        ("L", ctypes.c_double), ("qam_bits", ctypes.c_int),
+    ]
+
+
+class RaproError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str):
+        super().__init__(f"{what}: status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load librapro.so (once) and declare the entry points' signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1802_05427_gb300._build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "rapro_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "rapro_last_error": ([], ctypes.c_char_p),
+        "rapro_params_validate": ([ctypes.POINTER(RaproParams)], ctypes.c_int),
+        "rapro_build_weights_host": ([ctypes.POINTER(RaproParams), ctypes.c_int, _P], ctypes.c_int),
+        "rapro_plan_create": ([ctypes.POINTER(RaproParams), ctypes.POINTER(_P)], ctypes.c_int),
+        "rapro_plan_destroy": ([_P], ctypes.c_int),
+        "rapro_plan_dims": ([_P, _P, _P, _P, _P], ctypes.c_int),
+        "rapro_plan_device_status": ([_P, ctypes.c_int, _P], ctypes.c_int),
+        "rapro_ce_ls": ([_P, _P, _P, _P, _P], ctypes.c_int),
+        "rapro_ce_lmmse_subblock": ([_P, _P, _P, _P, _P], ctypes.c_int),
+        "rapro_ce_ls_lmmse": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+        "rapro_mmse_detect": ([_P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+        "rapro_receive_subframe": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def header_functions(path: str = HEADER) -> list:
+    """Names of the functions include/rapro.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rapro_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status: int, what: str) -> None:
+    if status != RAPRO_OK:
+        raise RaproError(status, what, lib().rapro_last_error().decode())
+
+
+def make_params(*, M: int, K: int, n_sc: int, n_fft: int, subblock: int, sigma2: float,
+                qam_bits: int, n_sym: int = 14, n_pilot_sym: int = 2,
+                pilot_sym_idx: Optional[Sequence[int]] = None, pdp: int = RAPRO_PDP_EXP,
+                n_taps: int = 6, tau_rms: float = 4.0, L: float = 8.0,
+                pilot_layout: int = RAPRO_PILOT_ORTHOGONAL) -> RaproParams:
+    """Build a rapro_params; by default each slot's pilot sits in its 4th symbol (3, 10)."""
+    p = RaproParams()
+    p.M, p.K, p.n_sc, p.n_fft = M, K, n_sc, n_fft
+    p.n_sym, p.n_pilot_sym = n_sym, n_pilot_sym
+    slot = n_sym // n_pilot_sym if n_pilot_sym else 1
+    idx = list(pilot_sym_idx) if pilot_sym_idx is not None else [j * slot + min(3, slot - 1)
+                                                                  for j in range(n_pilot_sym)]
+    for j, v in enumerate(idx[:RAPRO_MAX_PILOT_SYM]):
+        p.pilot_sym_idx[j] = v
+    p.pilot_layout, p.subblock, p.sigma2 = pilot_layout, subblock, sigma2
+    p.pdp, p.n_taps, p.tau_rms, p.L, p.qam_bits = pdp, n_taps, tau_rms, L, qam_bits
+    return p
+
+
+def rapro_params_validate(p: RaproParams) -> int:
+    return lib().rapro_params_validate(ctypes.byref(p))
+
+
+def rapro_build_weights_host(p: RaproParams, block_len: int):
+    """FP64 W of one block (numpy complex128 [block_len][block_len])."""
+    import numpy as np
+    buf = np.zeros(2 * block_len * block_len, dtype=np.float64)
+    _check(lib().rapro_build_weights_host(ctypes.byref(p), block_len, buf.ctypes.data),
+           "rapro_build_weights_host")
+    return (buf[0::2] + 1j * buf[1::2]).reshape(block_len, block_len)
+
+
+class Plan:
+    """Owns a rapro_plan (weights on the device, workspace, status word)."""
+
+    def __init__(self, params: RaproParams):
+        self.params = params
+        h = _P()
+        _check(lib().rapro_plan_create(ctypes.byref(params), ctypes.byref(h)), "rapro_plan_create")
+        self.handle = h
+        T, D, nb, tail = (ctypes.c_int() for _ in range(4))
+        _check(lib().rapro_plan_dims(h, ctypes.byref(T), ctypes.byref(D), ctypes.byref(nb),
+                                     ctypes.byref(tail)), "rapro_plan_dims")
+        self.T, self.D, self.nb, self.tail = T.value, D.value, nb.value, tail.value
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _check(lib().rapro_plan_destroy(self.handle), "rapro_plan_destroy")
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_status(self, reset: bool = False) -> int:
+        v = ctypes.c_int()
+        _check(lib().rapro_plan_device_status(self.handle, int(reset), ctypes.byref(v)),
+               "rapro_plan_device_status")
+        return v.value
+
+    # shapes of the C-ABI arrays
+    def shapes(self) -> dict:
+        p = self.params
+        T, D, K, M, N, q = self.T, self.D, p.K, p.M, p.n_sc, p.qam_bits
+        return dict(y_pilot=(T, K, M, N), pilots=(T, K, N), y_data=(T * D, M, N), h=(T, K, M, N),
+                    x_eq=(T * D, K, N), labels=(T * D, K, N), llr=(T * D, K, N, q), info=(T, N))
+
+
+def _ptr(t, shape, dtype, name):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def rapro_ce_ls(plan: Plan, y_pilot, pilots, h_ls, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    _check(lib().rapro_ce_ls(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
+                             _ptr(pilots, s["pilots"], c64, "pilots"), _ptr(h_ls, s["h"], c64, "h_ls"),
+                             _stream(stream)), "rapro_ce_ls")
+
+
+def rapro_ce_lmmse_subblock(plan: Plan, h_ls, h, w_override=None, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    _check(lib().rapro_ce_lmmse_subblock(plan.handle, _ptr(h_ls, s["h"], c64, "h_ls"),
+                                         _w_override(plan, w_override),
+                                         _ptr(h, s["h"], c64, "h"), _stream(stream)),
+           "rapro_ce_lmmse_subblock")
+
+
+def _w_override(plan: Plan, w_override):
+    import torch
+    if w_override is None:
+        return None
+    B, tail, nb = plan.params.subblock, plan.tail, plan.nb
+    n_w = (nb - (1 if tail else 0)) * B * B + tail * tail
+    return _ptr(w_override, (n_w,), torch.complex64, "w_override")
+
+
+def rapro_ce_ls_lmmse(plan: Plan, y_pilot, pilots, h, w_override=None, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    _check(lib().rapro_ce_ls_lmmse(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
+                                   _ptr(pilots, s["pilots"], c64, "pilots"), _w_override(plan, w_override),
+                                   _ptr(h, s["h"], c64, "h"), _stream(stream)), "rapro_ce_ls_lmmse")
+
+
+def rapro_mmse_detect(plan: Plan, h, y_data, x_eq, labels=None, llr=None, info=None, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    _check(lib().rapro_mmse_detect(plan.handle, _ptr(h, s["h"], c64, "h"),
+                                   _ptr(y_data, s["y_data"], c64, "y_data"),
+                                   _ptr(x_eq, s["x_eq"], c64, "x_eq"),
+                                   _ptr(labels, s["labels"], torch.uint8, "labels"),
+                                   _ptr(llr, s["llr"], torch.float32, "llr"),
+                                   _ptr(info, s["info"], torch.int32, "info"), _stream(stream)),
+           "rapro_mmse_detect")
+
+
+def rapro_receive_subframe(plan: Plan, y_pilot, pilots, y_data, x_eq, labels=None, llr=None,
+                           info=None, h_out=None, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    _check(lib().rapro_receive_subframe(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
+                                        _ptr(pilots, s["pilots"], c64, "pilots"),
+                                        _ptr(y_data, s["y_data"], c64, "y_data"),
+                                        _ptr(h_out, s["h"], c64, "h_out"),
+                                        _ptr(x_eq, s["x_eq"], c64, "x_eq"),
+                                        _ptr(labels, s["labels"], torch.uint8, "labels"),
+                                        _ptr(llr, s["llr"], torch.float32, "llr"),
+                                        _ptr(info, s["info"], torch.int32, "info"), _stream(stream)),
+           "rapro_receive_subframe")
+
+
+class Receiver:
+    """A plan plus device buffers for one subframe: the call a user makes with host data.
+
+    ``receive_host`` copies pinned host inputs to the device, runs rapro_receive_subframe
+    and copies the equalised symbols and labels back, all on one stream.
+    """
+
+    def __init__(self, params: RaproParams, device: int = 0, want_llr: bool = False):
+        import torch
+        torch.cuda.set_device(device)
+        self.plan = Plan(params)
+        s = self.plan.shapes()
+        dev = torch.device("cuda", device)
+        self.dev = dev
+        self.y_pilot = torch.empty(s["y_pilot"], dtype=torch.complex64, device=dev)
+        self.pilots = torch.empty(s["pilots"], dtype=torch.complex64, device=dev)
+        self.y_data = torch.empty(s["y_data"], dtype=torch.complex64, device=dev)
+        self.x_eq = torch.empty(s["x_eq"], dtype=torch.complex64, device=dev)
+        self.labels = torch.empty(s["labels"], dtype=torch.uint8, device=dev)
+        self.llr = torch.empty(s["llr"], dtype=torch.float32, device=dev) if want_llr else None
+        self.info = torch.empty(s["info"], dtype=torch.int32, device=dev)
+
+    def run_device(self, stream=None) -> None:
+        rapro_receive_subframe(self.plan, self.y_pilot, self.pilots, self.y_data, self.x_eq,
+                               self.labels, self.llr, self.info, stream=stream)
+
+    def receive_host(self, y_pilot_h, pilots_h, y_data_h, x_eq_h, labels_h, stream=None) -> None:
+        self.y_pilot.copy_(y_pilot_h, non_blocking=True)
+        self.pilots.copy_(pilots_h, non_blocking=True)
+        self.y_data.copy_(y_data_h, non_blocking=True)
+        self.run_device(stream)
+        x_eq_h.copy_(self.x_eq, non_blocking=True)
+        labels_h.copy_(self.labels, non_blocking=True)

@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Both sides read the same complex64 inputs.  Bars (FP32 device arithmetic):
+  * channel estimates and equalised symbols: norm-wise relative error <= 1e-5 per
+    (slot, user) resp. (data symbol, user);
+  * hard decisions identical wherever the oracle's unbiased symbol is farther than
+    1e-4 d_min/2 from a decision boundary; elsewhere the device label must still be a
+    nearest point within that tolerance;
+  * LLRs within 1e-4 relative plus the absolute error that a 1e-5 relative error of
+    x^ produces through the piecewise-linear max-log metric: 4 (2^m - 1) 1e-5 |x^|_s / (nu s)
+    (s = lattice scale, m bits per dimension);
+  * info == 0 unless a pivot is not positive and finite.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import rapro_oracle as O
+from paper_1802_05427_gb300 import _build, synth
+from paper_1802_05427_gb300 import rapro as R
+
+from _common import params_for, oracle_r, rel_err_per
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    _build.build()
+    R.lib()
+    torch.cuda.set_device(0)
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda") if dtype is None else t.to("cuda", dtype=dtype)
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _inputs(sh, seed):
+    sf = synth.make_subframe(sh, seed=seed)
+    return sf, {k: synth.as_c64(sf[k]) for k in ("y_pilot", "pilots", "y_data")}
+
+
+def gpu_receive(sh, c64, B, pdp="exp", h_out=True):
+    plan = R.Plan(params_for(sh, B, pdp=pdp))
+    s = plan.shapes()
+    yp, pil, yd = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"])
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+    lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
+    llr = torch.empty(s["llr"], dtype=torch.float32, device="cuda")
+    info = torch.full(s["info"], -7, dtype=torch.int32, device="cuda")
+    h = torch.empty(s["h"], dtype=torch.complex64, device="cuda") if h_out else None
+    R.rapro_receive_subframe(plan, yp, pil, yd, x, lab, llr, info, h_out=h)
+    out = dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr), info=_host(info))
+    if h_out:
+        out["h"] = _host(h)
+    assert plan.device_status() == 0
+    plan.close()
+    return out
+
+
+def oracle_receive(sh, c64, B, pdp="exp"):
+    return O.receive_subframe(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128),
+                              c64["y_data"].astype(np.complex128), B=B, sigma2=sh.sigma2,
+                              r=oracle_r(sh, pdp), n_data_per_slot=sh.n_data_per_slot, q=sh.qam_bits)
+
+
+def check_detection(g, o, q):
+    e = rel_err_per(g["x_eq"], o["x_eq"], axes=(2,))
+    assert e.max() <= TOL, f"x_eq rel err {e.max():.3g}"
+    margin = O.boundary_margin(o["xhat"], q)
+    safe = margin > MARGIN
+    bad = (g["labels"] != o["labels"]) & safe
+    assert not bad.any(), f"{bad.sum()} hard decisions differ away from boundaries"
+    # near a boundary the device label must still be a nearest point (within tolerance)
+    pts = O.constellation(q)
+    near = ~safe
+    if near.any():
+        xh = o["xhat"][near]
+        dmin = np.min(np.abs(xh[:, None] - pts[None]) ** 2, axis=1)
+        dg = np.abs(xh - pts[g["labels"][near].astype(int)]) ** 2
+        assert np.all(dg - dmin <= 1e-6 * (1 + np.abs(xh) ** 2))
+    assert near.mean() < 1e-3
+    m = q // 2
+    s = np.sqrt(2.0 * (4 ** m - 1) / 3.0)
+    xmag = np.maximum(1.0, np.abs(o["xhat"]))[..., None]
+    tol = 1e-4 * np.abs(o["llr"]) + 4 * (2 ** m - 1) * 10 * TOL * xmag / (o["nu"][..., None] * s)
+    err = np.abs(g["llr"] - o["llr"])
+    assert np.all(err <= tol), f"llr worst excess {np.max(err - tol):.3g}"
+    # LLR signs agree with the device's own hard bits
+    bits = (g["labels"][..., None] >> (q - 1 - np.arange(q))) & 1
+    nz = np.abs(g["llr"]) > 0
+    assert np.all((g["llr"][nz] > 0) == (bits[nz] == 0))
+
+
+# ------------------------------------------------------------------------ LS
+@pytest.mark.parametrize("dims", [(8, 2, 72), (20, 5, 100), (3, 1, 75), (128, 12, 1200)])
+def test_ls_parity(dims):
+    M, K, N = dims
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=max(128, 2 * N), qam_bits=2)
+    sf, c64 = _inputs(sh, 1)
+    plan = R.Plan(params_for(sh, min(12, N)))
+    h = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
+    R.rapro_ce_ls(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), h)
+    ref = O.ls_estimate(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128))
+    assert rel_err_per(_host(h), ref, axes=(2, 3)).max() <= 1e-6
+
+
+# --------------------------------------------------------------------- LMMSE
+LMMSE_CASES = [
+    # M, K, N, n_fft, B
+    (8, 2, 72, 128, 12), (8, 2, 72, 128, 1), (8, 2, 72, 128, 72), (5, 3, 100, 256, 12),
+    (5, 3, 100, 256, 7), (4, 2, 130, 256, 33), (4, 2, 130, 256, 48), (4, 2, 200, 256, 100),
+    (6, 2, 75, 128, 16), (3, 2, 90, 128, 24), (3, 2, 96, 128, 32), (2, 1, 64, 128, 4),
+    (128, 12, 1200, 2048, 12), (128, 12, 1200, 2048, 48), (128, 12, 1200, 2048, 100),
+    (128, 12, 1200, 2048, 1200),
+]
+
+
+@pytest.mark.parametrize("case", LMMSE_CASES)
+def test_lmmse_parity(case):
+    M, K, N, nfft, B = case
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=24 if nfft >= 2048 else 6,
+                             tau_rms=8.0 if nfft >= 2048 else 4.0, snr_db=10.0, qam_bits=2)
+    sf, c64 = _inputs(sh, 2)
+    h_ls = synth.as_c64(O.ls_estimate(c64["y_pilot"], c64["pilots"]))
+    plan = R.Plan(params_for(sh, B))
+    h = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
+    R.rapro_ce_lmmse_subblock(plan, _dev(h_ls), h)
+    ref = O.subblock_lmmse(h_ls.astype(np.complex128), B, oracle_r(sh), sh.sigma2)
+    e = rel_err_per(_host(h), ref, axes=(2, 3))
+    assert e.max() <= TOL, e.max()
+
+
+@pytest.mark.parametrize("B", [12, 40])
+def test_lmmse_weight_override(B):
+    """w_override: one W per block (here random), applied block by block (Eq. 12)."""
+    sh = synth.SubframeShape(M=6, K=2, n_sc=100, n_fft=256, qam_bits=2)
+    sf, c64 = _inputs(sh, 3)
+    h_ls = synth.as_c64(O.ls_estimate(c64["y_pilot"], c64["pilots"]))
+    plan = R.Plan(params_for(sh, B))
+    rng = np.random.default_rng(5)
+    weights, flat = [], []
+    for b0 in range(0, sh.n_sc, B):
+        n = min(B, sh.n_sc - b0)
+        W = synth.as_c64((rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / n)
+        weights.append((b0, W.astype(np.complex128)))
+        flat.append(W.ravel())
+    h = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
+    R.rapro_ce_lmmse_subblock(plan, _dev(h_ls), h, w_override=_dev(np.concatenate(flat)))
+    ref = O.subblock_lmmse(h_ls.astype(np.complex128), B, None, None, weights=weights)
+    assert rel_err_per(_host(h), ref, axes=(2, 3)).max() <= TOL
+
+
+# ----------------------------------------------------------------- detection
+DETECT_CASES = [
+    # M, K, N, D, q
+    (8, 2, 72, 6, 2), (20, 5, 100, 6, 4), (128, 12, 1200, 6, 4), (64, 16, 96, 12, 6),
+    (1, 1, 40, 6, 2), (3, 3, 33, 6, 2), (16, 7, 75, 5, 6), (36, 12, 48, 1, 4), (9, 4, 16, 12, 2),
+]
+
+
+@pytest.mark.parametrize("case", DETECT_CASES)
+def test_detect_parity(case):
+    M, K, N, D, q = case
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=max(128, 2 * N), qam_bits=q, n_data_per_slot=D,
+                             snr_db=15.0)
+    sf, c64 = _inputs(sh, 4)
+    h = synth.as_c64(O.subblock_lmmse(O.ls_estimate(c64["y_pilot"], c64["pilots"]), min(12, N),
+                                      oracle_r(sh), sh.sigma2))
+    plan = R.Plan(params_for(sh, min(12, N)))
+    s = plan.shapes()
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+    lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
+    llr = torch.empty(s["llr"], dtype=torch.float32, device="cuda")
+    info = torch.full(s["info"], -1, dtype=torch.int32, device="cuda")
+    R.rapro_mmse_detect(plan, _dev(h), _dev(c64["y_data"]), x, lab, llr, info)
+    x_o, s_o = O.mmse_detect(h.astype(np.complex128), c64["y_data"].astype(np.complex128), sh.sigma2, D)
+    xhat, nu = O.unbias(x_o, s_o, D)
+    o = dict(x_eq=x_o, xhat=xhat, nu=nu, labels=O.hard_decision(xhat, q), llr=O.maxlog_llr(xhat, nu, q))
+    g = dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr))
+    check_detection(g, o, q)
+    assert np.all(_host(info) == 0)
+    assert plan.device_status() == 0
+
+
+def test_detect_optional_outputs_may_be_null():
+    sh = synth.SubframeShape(M=8, K=3, n_sc=40, n_fft=128, qam_bits=4)
+    sf, c64 = _inputs(sh, 6)
+    h = synth.as_c64(O.ls_estimate(c64["y_pilot"], c64["pilots"]))
+    plan = R.Plan(params_for(sh, 8))
+    x = torch.empty(plan.shapes()["x_eq"], dtype=torch.complex64, device="cuda")
+    R.rapro_mmse_detect(plan, _dev(h), _dev(c64["y_data"]), x)
+    x_o, _ = O.mmse_detect(h.astype(np.complex128), c64["y_data"].astype(np.complex128), sh.sigma2, 6)
+    assert rel_err_per(_host(x), x_o, axes=(2,)).max() <= TOL
+
+
+def test_nan_subcarrier_sets_info_and_spares_the_rest():
+    """A non-finite channel estimate makes pivot 1 fail on that subcarrier only."""
+    sh = synth.SubframeShape(M=8, K=3, n_sc=40, n_fft=128, qam_bits=2)
+    sf, c64 = _inputs(sh, 7)
+    h = synth.as_c64(O.ls_estimate(c64["y_pilot"], c64["pilots"]))
+    h[1, :, :, 17] = np.nan
+    plan = R.Plan(params_for(sh, 8))
+    s = plan.shapes()
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+    info = torch.full(s["info"], -1, dtype=torch.int32, device="cuda")
+    R.rapro_mmse_detect(plan, _dev(h), _dev(c64["y_data"]), x, info=info)
+    inf_h, x_h = _host(info), _host(x)
+    assert inf_h[1, 17] == 1
+    assert np.count_nonzero(inf_h) == 1
+    assert np.isnan(x_h[6:12, :, 17]).all()
+    good = np.ones(sh.n_sc, bool)
+    good[17] = False
+    x_o, _ = O.mmse_detect(h[:1].astype(np.complex128), c64["y_data"][:6].astype(np.complex128), sh.sigma2, 6)
+    assert rel_err_per(x_h[:6], x_o, axes=(2,)).max() <= TOL
+    assert np.isfinite(x_h[6:12][..., good]).all()
+
+
+# ------------------------------------------------------------- whole receive
+RECEIVE_CASES = [
+    ("tiny", synth.TINY, 12, 0), ("ragged", synth.SubframeShape(M=20, K=5, n_sc=100, n_fft=256, n_taps=6,
+                                                                 tau_rms=4.0, snr_db=12.0, qam_bits=4), 12, 1),
+    ("odd_nsc", synth.SubframeShape(M=12, K=4, n_sc=75, n_fft=128, snr_db=8.0, qam_bits=2), 10, 2),
+]
+
+
+@pytest.mark.parametrize("name,sh,B,seed", RECEIVE_CASES, ids=[c[0] for c in RECEIVE_CASES])
+def test_receive_subframe_parity_small(name, sh, B, seed):
+    sf, c64 = _inputs(sh, synth.SEED_BASE + seed)
+    g = gpu_receive(sh, c64, B)
+    o = oracle_receive(sh, c64, B)
+    assert rel_err_per(g["h"], o["h"], axes=(2, 3)).max() <= TOL
+    check_detection(g, o, sh.qam_bits)
+    assert np.all(g["info"] == 0)
+
+
+@pytest.mark.parametrize("snr", [0.0, 10.0, 20.0])
+@pytest.mark.parametrize("B", [12, 48, 100, 1200])
+def test_receive_subframe_parity_paper_scale(B, snr):
+    """M = 128, K = 12, 1200 subcarriers, 16-QAM, 24-tap exponential PDP (the headline
+    workload), every output compared in full."""
+    sh = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "snr_db": snr})
+    sf, c64 = _inputs(sh, synth.SEED_BASE + 1)
+    g = gpu_receive(sh, c64, B)
+    o = oracle_receive(sh, c64, B)
+    assert rel_err_per(g["h"], o["h"], axes=(2, 3)).max() <= TOL
+    check_detection(g, o, sh.qam_bits)
+    assert np.all(g["info"] == 0)
+
+
+def test_receive_without_h_out_and_uniform_L_model():
+    sh = synth.SubframeShape(M=16, K=4, n_sc=96, n_fft=256, snr_db=15.0, qam_bits=6)
+    sf, c64 = _inputs(sh, 11)
+    g = gpu_receive(sh, c64, 12, pdp="uniform_L", h_out=False)
+    o = oracle_receive(sh, c64, 12, pdp="uniform_L")
+    check_detection(g, o, sh.qam_bits)
+
+
+def test_invalid_pointers_are_rejected_without_launch():
+    sh = synth.TINY
+    plan = R.Plan(params_for(sh, 12))
+    lib = R.lib()
+    assert lib.rapro_ce_ls(plan.handle, None, None, None, None) == R.RAPRO_ERR_INVALID_ARG
+    assert lib.rapro_mmse_detect(plan.handle, None, None, None, None, None, None, None) == R.RAPRO_ERR_INVALID_ARG
+    assert lib.rapro_receive_subframe(None, None, None, None, None, None, None, None, None, None) == \
+        R.RAPRO_ERR_INVALID_ARG
+    x = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
+    assert lib.rapro_ce_lmmse_subblock(plan.handle, x.data_ptr(), None, x.data_ptr(), None) == \
+        R.RAPRO_ERR_INVALID_ARG
+    assert plan.device_status() == 0
