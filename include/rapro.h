@@ -198,6 +198,35 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
                                     rapro_c32* h_out, rapro_c32* x_eq, uint8_t* labels,
                                     float* llr, int32_t* info, rapro_stream stream);
 
+/*
+ * Allocation-free variant of rapro_receive_subframe (the paper has no counterpart; it
+ * runs its receiver on host memory it allocates freely).  For callers that cannot
+ * allocate device memory when a subframe arrives: code running inside a CUDA graph
+ * capture (where cudaMalloc is not allowed), real-time slot loops that must not wait on an
+ * allocator, and processes whose device memory belongs to another framework's pool.
+ *  - Needs no plan: p is validated and the weights of its sub-block size are built in
+ *    FP64 on the host at every call and passed to the kernel as parameters, so subblock
+ *    must be <= 32 (RAPRO_ERR_UNSUPPORTED otherwise).
+ *  - The channel-estimate scratch is a fixed 32 MiB device array inside the library
+ *    (held by every GPU that loads the library until the process exits):
+ *    n_pilot_sym * K * M * n_sc * 8 bytes must not exceed 32 MiB (RAPRO_ERR_INVALID_ARG
+ *    otherwise; the 128 x 12 x 1200 two-slot subframe needs 29.5 MB).
+ *  - Allocates and frees no device memory; the only host allocation is the text of an
+ *    error message on a rejected call.
+ *  - The first call on a device looks up the scratch's device address and raises the
+ *    detector's shared-memory limit; make that first call before any stream capture.
+ *  - All calls share the scratch (it keeps the last call's contents): calls that overlap
+ *    on the GPU race and give undefined outputs; serialise them.
+ *  - A pipeline timeout leaves a subcarrier's outputs and info entry unwritten: a caller
+ *    that must detect it fills info with a sentinel (e.g. -1) before the call.
+ * Inputs, outputs, layouts and results are those of rapro_receive_subframe with
+ * h_out == NULL, on the caller's stream.
+ */
+rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, const rapro_c32* y_pilot,
+                                            const rapro_c32* pilots, const rapro_c32* y_data,
+                                            rapro_c32* x_eq, uint8_t* labels, float* llr,
+                                            int32_t* info, rapro_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -385,6 +385,31 @@ cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, floa
   return cudaGetLastError();
 }
 
+// Detection without a plan (same kernel): used by the allocation-free receive entry point.
+cudaError_t launch_detect_raw(const DetTiles& tiles, int T, int K, int M, int N, int D, int q,
+                              float sigma2, int* status, const float2* h, const float2* y,
+                              float2* x_eq, unsigned char* labels, float* llr, int* info,
+                              cudaStream_t st) {
+  DetParams P;
+  P.T = T; P.K = K; P.M = M; P.N = N; P.D = D; P.q = q;
+  P.sigma2 = sigma2;
+  P.nchunks = (M + DET_MCH - 1) / DET_MCH;
+  P.tiles = tiles;
+  P.status = status;
+  CUtensorMap mh{}, my{};
+  const bool aligned = ((reinterpret_cast<uintptr_t>(h) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+  bool tma = aligned && (N % 2 == 0) && encode_map(&mh, h, N, M, T * K, K) &&
+             encode_map(&my, y, N, M, T * D, D);
+  const size_t smem = detect_smem_bytes(tiles, tma);
+  dim3 grid((N + DET_SC - 1) / DET_SC, T);
+  dim3 block(32 * tiles.n_tiles);
+  if (tma)
+    detect_kernel<true><<<grid, block, smem, st>>>(mh, my, h, y, x_eq, labels, llr, info, P);
+  else
+    detect_kernel<false><<<grid, block, smem, st>>>(mh, my, h, y, x_eq, labels, llr, info, P);
+  return cudaGetLastError();
+}
+
 // Raise the dynamic shared-memory limit of the detector once per device, at plan
 // creation (not at launch, which may be inside a CUDA-graph capture).
 cudaError_t prepare_detect(int device) {

@@ -204,6 +204,36 @@ static cudaError_t launch_tiled(const Plan& pl, const float2* x, const float2* p
   return cudaGetLastError();
 }
 
+// Small-block LS + LMMSE without a plan: host weights w_main (B x B) and w_tail
+// (tail x tail), row-major.  Used by the allocation-free receive entry point.
+template <int BM>
+static cudaError_t launch_small_raw(const float2* w_main, const float2* w_tail, int B, int tail,
+                                    int nb, int rows, int M, int N, const float2* y,
+                                    const float2* pil, float2* out, cudaStream_t st) {
+  WSmall<BM> W;
+  for (int i = 0; i < BM * BM; ++i) W.w[i] = W.wt[i] = make_float2(0.f, 0.f);
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) W.w[i * BM + j] = w_main[i * B + j];
+  for (int i = 0; i < tail; ++i)
+    for (int j = 0; j < tail; ++j) W.wt[i * BM + j] = w_tail[i * tail + j];
+  dim3 grid((rows + 127) / 128, nb);
+  lmmse_small_kernel<BM, true><<<grid, 128, 0, st>>>(y, pil, out, rows, M, N, B, nb, tail, W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ls_lmmse_small_raw(const float2* w_main, const float2* w_tail, int B, int tail,
+                                      int nb, int rows, int M, int N, const float2* y,
+                                      const float2* pil, float2* out, cudaStream_t st) {
+  if (B <= 4) return launch_small_raw<4>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+  if (B <= 8) return launch_small_raw<8>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+  if (B <= 12) return launch_small_raw<12>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+  if (B <= 16) return launch_small_raw<16>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+  if (B <= 24) return launch_small_raw<24>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+  if (B <= LMMSE_SMALL_MAX)
+    return launch_small_raw<32>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
                          const float2* d_w_main, const float2* d_w_tail,
                          const float2* /*h_w_main*/, const float2* /*h_w_tail*/, float2* out,

@@ -1,0 +1,168 @@
+// Allocation-free receive: rapro_receive_subframe_noalloc.
+//
+// Some callers cannot allocate device memory at the moment they receive a subframe:
+// code that runs while a CUDA graph is being captured (cudaMalloc is not allowed inside a
+// capture), real-time slot loops that must never wait on an allocator (the receiver has
+// a fixed per-slot deadline), and processes whose device memory is owned by another
+// framework's pool.  For them this entry point needs no plan and allocates nothing: the
+// channel-estimate scratch that rapro_receive_subframe keeps in its plan lives here in a
+// fixed, file-scope device array instead, and the LMMSE weights travel in the kernel
+// parameters.
+//
+// The array (kNoAllocScratchBytes) is part of the library's device image: every GPU that
+// loads the library holds it until the process exits.  All calls share it and it keeps
+// the last call's contents, so calls that overlap on the GPU (different streams, or
+// different host threads on the same device) race on it.
+#include <cmath>
+#include <complex>
+#include <mutex>
+
+#include "rapro_internal.h"
+
+namespace rapro {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;     // 32 MiB of channel estimate
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) float2 g_noalloc_h[kNoAllocScratchBytes / sizeof(float2)];
+static __device__ __align__(256) int g_noalloc_status;
+
+struct DeviceScratch {
+  float2* h = nullptr;
+  int* status = nullptr;
+  cudaError_t err = cudaSuccess;
+};
+DeviceScratch g_scratch[kMaxDevices];
+std::once_flag g_once[kMaxDevices];
+
+// Once per device, with that device current: the device addresses of the arrays (their
+// names are host-side stand-ins in host code) and the detector's shared-memory limit.
+const DeviceScratch& device_scratch(int dev) {
+  std::call_once(g_once[dev], [dev] {
+    DeviceScratch& s = g_scratch[dev];
+    s.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.h), g_noalloc_h);
+    if (s.err == cudaSuccess) s.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.status), g_noalloc_status);
+    if (s.err == cudaSuccess) s.err = prepare_detect(dev);
+  });
+  return g_scratch[dev];
+}
+
+using cd = std::complex<double>;
+
+cd corr_model(const rapro_params& p, int d) {
+  const double two_pi = 6.283185307179586476925286766559;
+  if (p.pdp == RAPRO_PDP_EXP) {
+    double norm = 0.0;
+    for (int l = 0; l < p.n_taps; ++l) norm += std::exp(-l / p.tau_rms);
+    cd acc(0.0, 0.0);
+    for (int l = 0; l < p.n_taps; ++l) {
+      const double ph = -two_pi * double(l) * double(d) / double(p.n_fft);
+      acc += (std::exp(-l / p.tau_rms) / norm) * cd(std::cos(ph), std::sin(ph));
+    }
+    return acc;
+  }
+  if (d == 0) return cd(1.0, 0.0);
+  const double x = two_pi * p.L * double(d) / double(p.n_fft);
+  const cd num(1.0 - std::cos(x), std::sin(x));
+  return num / cd(0.0, x);
+}
+
+// FP64 weights W = R (R + sigma2 I)^-1 of one block of n <= LMMSE_SMALL_MAX subcarriers,
+// on the stack: Cholesky A = L L^H, X = A^-1 R by two triangular solves, W = X^H, rounded
+// to complex64 (the same operation order as the plan's builder).
+bool small_weights(const rapro_params& p, int n, float2* w) {
+  constexpr int NM = LMMSE_SMALL_MAX;
+  cd r[2 * NM - 1], L[NM * NM], X[NM * NM], y[NM];
+  for (int d = -(n - 1); d <= n - 1; ++d) r[d + n - 1] = corr_model(p, d);
+  auto R = [&](int a, int b) { return r[a - b + n - 1]; };
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) L[i * n + j] = R(i, j) + (i == j ? p.sigma2 : 0.0);
+  for (int j = 0; j < n; ++j) {
+    cd* Lj = &L[j * n];
+    double d = Lj[j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(Lj[k]);
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    const double ljj = std::sqrt(d);
+    Lj[j] = cd(ljj, 0.0);
+    for (int i = j + 1; i < n; ++i) {
+      cd* Li = &L[i * n];
+      cd s = Li[j];
+      for (int k = 0; k < j; ++k) s -= Li[k] * std::conj(Lj[k]);
+      Li[j] = s / ljj;
+    }
+  }
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      cd s = R(i, c);
+      const cd* Li = &L[i * n];
+      for (int k = 0; k < i; ++k) s -= Li[k] * y[k];
+      y[i] = s / Li[i].real();
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      cd s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= std::conj(L[k * n + i]) * X[k * n + c];
+      X[i * n + c] = s / L[i * n + i].real();
+    }
+  }
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      const cd v = std::conj(X[b * n + a]);
+      w[a * n + b] = make_float2(float(v.real()), float(v.imag()));
+    }
+  return true;
+}
+
+rapro_status reject(rapro_status s, const char* msg) {
+  set_error(msg);
+  return s;
+}
+
+}  // namespace
+}  // namespace rapro
+
+using namespace rapro;
+
+extern "C" rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, const rapro_c32* y_pilot,
+                                                       const rapro_c32* pilots, const rapro_c32* y_data,
+                                                       rapro_c32* x_eq, uint8_t* labels, float* llr,
+                                                       int32_t* info, rapro_stream stream) {
+  rapro_status s = rapro_params_validate(p);
+  if (s != RAPRO_OK) return s;
+  if (!y_pilot || !pilots || !y_data || !x_eq)
+    return reject(RAPRO_ERR_INVALID_ARG, "y_pilot, pilots, y_data and x_eq must not be NULL");
+  if (p->subblock > LMMSE_SMALL_MAX)
+    return reject(RAPRO_ERR_UNSUPPORTED, "the allocation-free receive needs subblock <= 32");
+  const int T = p->n_pilot_sym, D = p->n_sym / p->n_pilot_sym - 1;
+  const size_t h_bytes = size_t(T) * p->K * p->M * p->n_sc * sizeof(float2);
+  if (h_bytes > kNoAllocScratchBytes)
+    return reject(RAPRO_ERR_INVALID_ARG,
+                  "n_pilot_sym*K*M*n_sc*8 bytes exceeds the 32 MiB scratch of the allocation-free receive");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return reject(RAPRO_ERR_INVALID_ARG, "device index out of range");
+  const DeviceScratch& ds = device_scratch(dev);
+  if (ds.err != cudaSuccess) return cuda_fail(ds.err, "allocation-free receive set-up");
+
+  const int B = p->subblock, tail = p->n_sc % p->subblock, nb = (p->n_sc + B - 1) / B;
+  float2 w_main[LMMSE_SMALL_MAX * LMMSE_SMALL_MAX], w_tail[LMMSE_SMALL_MAX * LMMSE_SMALL_MAX];
+  if (!small_weights(*p, B, w_main) || (tail && !small_weights(*p, tail, w_tail)))
+    return reject(RAPRO_ERR_NOT_POSDEF, "R_b + sigma2 I is not positive definite in FP64");
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // The status word only has to start at zero; the estimate is fully rewritten below.
+  if ((e = cudaMemsetAsync(ds.status, 0, sizeof(int), st)) != cudaSuccess)
+    return cuda_fail(e, "clear status word");
+  const float2* yp = reinterpret_cast<const float2*>(y_pilot);
+  const float2* pil = reinterpret_cast<const float2*>(pilots);
+  e = launch_ls_lmmse_small_raw(w_main, w_tail, B, tail, nb, T * p->K * p->M, p->M, p->n_sc, yp, pil,
+                                ds.h, st);
+  if (e != cudaSuccess) return cuda_fail(e, "LS+LMMSE kernel launch");
+  const DetTiles tiles = make_det_tiles(p->K, D);
+  e = launch_detect_raw(tiles, T, p->K, p->M, p->n_sc, D, p->qam_bits, float(p->sigma2), ds.status, ds.h,
+                        reinterpret_cast<const float2*>(y_data), reinterpret_cast<float2*>(x_eq), labels, llr,
+                        info, st);
+  if (e != cudaSuccess) return cuda_fail(e, "detection kernel launch");
+  return RAPRO_OK;
+}

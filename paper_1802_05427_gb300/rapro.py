@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
         "rapro_ce_ls_lmmse": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
         "rapro_mmse_detect": ([_P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
         "rapro_receive_subframe": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+        "rapro_receive_subframe_noalloc": ([ctypes.POINTER(RaproParams), _P, _P, _P, _P, _P, _P, _P, _P],
+                                           ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -250,6 +252,21 @@ def rapro_receive_subframe(plan: Plan, y_pilot, pilots, y_data, x_eq, labels=Non
                                         _ptr(llr, s["llr"], torch.float32, "llr"),
                                         _ptr(info, s["info"], torch.int32, "info"), _stream(stream)),
            "rapro_receive_subframe")
+
+
+def rapro_receive_subframe_noalloc(params: RaproParams, y_pilot, pilots, y_data, x_eq, labels=None,
+                                   llr=None, info=None, stream=None) -> None:
+    """The allocation-free receive: no plan, the library's fixed device scratch (see rapro.h)."""
+    import torch
+    p = params
+    T, D = p.n_pilot_sym, p.n_sym // p.n_pilot_sym - 1
+    K, M, N, q = p.K, p.M, p.n_sc, p.qam_bits
+    c64 = torch.complex64
+    _check(lib().rapro_receive_subframe_noalloc(
+        ctypes.byref(p), _ptr(y_pilot, (T, K, M, N), c64, "y_pilot"), _ptr(pilots, (T, K, N), c64, "pilots"),
+        _ptr(y_data, (T * D, M, N), c64, "y_data"), _ptr(x_eq, (T * D, K, N), c64, "x_eq"),
+        _ptr(labels, (T * D, K, N), torch.uint8, "labels"), _ptr(llr, (T * D, K, N, q), torch.float32, "llr"),
+        _ptr(info, (T, N), torch.int32, "info"), _stream(stream)), "rapro_receive_subframe_noalloc")
 
 
 class Receiver:
