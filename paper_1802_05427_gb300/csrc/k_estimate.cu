@@ -5,6 +5,7 @@
 // The filter is out[r][blk] = W_b * in[r][blk]: for every block a complex
 // (rows x B_b) x (B_b x B_b)^T product, FP32 FFMA with FP32 accumulation.
 #include <algorithm>
+#include <mutex>
 
 #include "rapro_internal.h"
 #include "rapro_ptx.cuh"
@@ -35,9 +36,15 @@ cudaError_t launch_ls(const float2* y, const float2* pil, float2* h, int T, int 
 }
 
 // ----------------------------------------------------- LMMSE, small blocks (B <= 32)
-// The block's weights travel in the kernel parameters, so every W[i][j] is a
-// constant-bank operand of the FFMAs and costs no load instruction.  One thread filters
-// one block of one row; lanes are consecutive rows, so pilots (same user) broadcast.
+// One CTA per segment of up to SEG_BLOCKS blocks of one row (t, s, m).  The segment's
+// subcarriers arrive with coalesced loads (LS applied on the way in) into shared memory,
+// one padded slot of BM + 1 entries per block (conflict-free per half-warp); each thread
+// then filters one block from registers with the weights in the kernel parameters, so
+// every W[i][j] is a constant-bank operand of the FFMAs, and writes it back in place; the
+// segment leaves with coalesced stores.
+constexpr int SEG_BLOCKS = 128;
+constexpr int SMALL_THREADS = 128;
+
 template <int BM>
 struct WSmall {
   float2 w[BM * BM];   // full-size block, zero padded to BM x BM
@@ -57,59 +64,216 @@ __device__ __forceinline__ void apply_w(const float2 (&W)[BM * BM], const float2
 }
 
 template <int BM, bool LS>
-__global__ void __launch_bounds__(256) lmmse_small_kernel(const float2* __restrict__ x,
-                                                          const float2* __restrict__ pil,
-                                                          float2* __restrict__ out, int rows,
-                                                          int M, int N, int B, int nb, int tail,
-                                                          const __grid_constant__ WSmall<BM> W) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (row >= rows) return;
-  const bool is_tail = (tail != 0) && (b == nb - 1);
-  const int Bb = is_tail ? tail : B;
-  const size_t base = size_t(row) * N + size_t(b) * B;
-  float2 v[BM];
-#pragma unroll
-  for (int j = 0; j < BM; ++j) v[j] = (j < Bb) ? x[base + j] : make_float2(0.f, 0.f);
-  if (LS) {
-    const size_t pb = size_t(row / M) * N + size_t(b) * B;
-#pragma unroll
-    for (int j = 0; j < BM; ++j) {
-      if (j < Bb) {
-        const float2 p = pil[pb + j];
+__global__ void __launch_bounds__(SMALL_THREADS) lmmse_small_kernel(const float2* __restrict__ x,
+                                                                    const float2* __restrict__ pil,
+                                                                    float2* __restrict__ out, int M, int N,
+                                                                    int B, int nb, int tail,
+                                                                    const __grid_constant__ WSmall<BM> W) {
+  __shared__ float2 xs[SEG_BLOCKS * (BM + 1)];
+  const int row = blockIdx.y;
+  const int b0 = blockIdx.x * SEG_BLOCKS;
+  const int nbl = min(SEG_BLOCKS, nb - b0);
+  const int e0 = b0 * B;
+  const int n_el = min(N - e0, nbl * B);
+  const float2* xr = x + size_t(row) * N + e0;
+  const float2* pr = pil + size_t(row / M) * N + e0;
+  float2* orow = out + size_t(row) * N + e0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int dblk = nt / B, dj = nt % B;
+
+  {  // element e of the segment -> (block e / B, offset e % B), tracked incrementally
+    int blk = tid / B, j = tid % B;
+#pragma unroll 4
+    for (int e = tid; e < n_el; e += nt) {
+      float2 v = xr[e];
+      if (LS) {
+        const float2 p = pr[e];
         const float inv = 1.0f / fmaf(p.x, p.x, p.y * p.y);
-        const float2 y = v[j];
-        v[j] = make_float2(fmaf(y.x, p.x, y.y * p.y) * inv, fmaf(y.y, p.x, -y.x * p.y) * inv);
+        v = make_float2(fmaf(v.x, p.x, v.y * p.y) * inv, fmaf(v.y, p.x, -v.x * p.y) * inv);
+      }
+      xs[blk * (BM + 1) + j] = v;
+      blk += dblk;
+      j += dj;
+      if (j >= B) { j -= B; ++blk; }
+    }
+  }
+  __syncthreads();
+  for (int bl = tid; bl < nbl; bl += nt) {
+    const int b = b0 + bl;
+    const bool is_tail = (tail != 0) && (b == nb - 1);
+    const int Bb = is_tail ? tail : B;
+    float2 v[BM], acc[BM];
+#pragma unroll
+    for (int j = 0; j < BM; ++j) v[j] = (j < Bb) ? xs[bl * (BM + 1) + j] : make_float2(0.f, 0.f);
+    if (!is_tail)
+      apply_w<BM>(W.w, v, acc);
+    else
+      apply_w<BM>(W.wt, v, acc);
+#pragma unroll
+    for (int i = 0; i < BM; ++i)
+      if (i < Bb) xs[bl * (BM + 1) + i] = acc[i];
+  }
+  __syncthreads();
+  {
+    int blk = tid / B, j = tid % B;
+#pragma unroll 4
+    for (int e = tid; e < n_el; e += nt) {
+      orow[e] = xs[blk * (BM + 1) + j];
+      blk += dblk;
+      j += dj;
+      if (j >= B) { j -= B; ++blk; }
+    }
+  }
+}
+
+// Streaming variant for rows that bulk copies can move (n_sc and B even, 16-byte aligned
+// arrays, at most STREAM_MAX_THREADS blocks per row): one CTA filters STREAM_ROWS
+// consecutive antenna rows of one (slot, user).  Its pilot row is loaded once and turned
+// into conj(p) / |p|^2; row buffers are filled and drained by 1-D bulk copies in a
+// STREAM_BUF-deep ring, so loads stay in flight while the CTA computes.  Thread b owns
+// block b of every row and keeps that block's pilot factors in registers.
+constexpr int STREAM_ROWS = 8;
+constexpr int STREAM_BUF = 3;
+constexpr int STREAM_MAX_THREADS = 512;
+
+template <int BM>
+__global__ void __launch_bounds__(STREAM_MAX_THREADS) lmmse_stream_kernel(
+    const float2* __restrict__ y, const float2* __restrict__ pil, float2* __restrict__ out, int M, int N,
+    int B, int nb, int tail, int* status, const __grid_constant__ WSmall<BM> W) {
+  static_assert(BM % 2 == 0, "blocks move as pairs of complex values");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);            // [0]: pilot, [1 + b]: row buffer b
+  int* s_abort = reinterpret_cast<int*>(smem + 64);
+  float2* pc = reinterpret_cast<float2*>(smem + 128);             // pilot row -> conj(p)/|p|^2
+  float2* buf = pc + N;                                          // [STREAM_BUF][N]
+  const int ts = blockIdx.y;                                     // t*K + s
+  const int m0 = blockIdx.x * STREAM_ROWS;
+  const int nrows = min(STREAM_ROWS, M - m0);
+  const size_t row0 = size_t(ts) * M + m0;
+  const uint32_t row_bytes = uint32_t(N) * sizeof(float2);
+  const int tid = threadIdx.x;
+
+  if (tid == 0) {
+    *s_abort = 0;
+    for (int b = 0; b <= STREAM_BUF; ++b) mbar_init(&bars[b], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bars[0], row_bytes);
+    bulk_load(pc, pil + size_t(ts) * N, row_bytes, &bars[0]);
+    for (int r = 0; r < STREAM_BUF && r < nrows; ++r) {
+      mbar_arrive_expect_tx(&bars[1 + r], row_bytes);
+      bulk_load(buf + size_t(r) * N, y + (row0 + r) * N, row_bytes, &bars[1 + r]);
+    }
+  }
+  const int b = tid;
+  const bool active = b < nb;
+  const bool is_tail = (tail != 0) && (b == nb - 1);
+  const int Bb = is_tail ? tail : B;                             // even
+  const int e0 = b * B;                                          // even
+  float2 pcr[BM];
+  if (!mbar_wait_bounded(&bars[0], 0)) atomicExch(s_abort, 1);
+#pragma unroll
+  for (int jp = 0; jp < BM / 2; ++jp) {
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active && 2 * jp < Bb) q = reinterpret_cast<const float4*>(pc + e0)[jp];
+    float inv = 1.0f / fmaf(q.x, q.x, q.y * q.y);
+    pcr[2 * jp] = (active && 2 * jp < Bb) ? make_float2(q.x * inv, -q.y * inv) : make_float2(0.f, 0.f);
+    inv = 1.0f / fmaf(q.z, q.z, q.w * q.w);
+    pcr[2 * jp + 1] = (active && 2 * jp < Bb) ? make_float2(q.z * inv, -q.w * inv) : make_float2(0.f, 0.f);
+  }
+  for (int r = 0; r < nrows; ++r) {
+    const int slot = r % STREAM_BUF;
+    float2* row = buf + size_t(slot) * N;
+    if (!mbar_wait_bounded(&bars[1 + slot], uint32_t(r / STREAM_BUF) & 1u)) atomicExch(s_abort, 1);
+    if (active) {
+      float2 v[BM], acc[BM];
+      float4* row4 = reinterpret_cast<float4*>(row + e0);
+#pragma unroll
+      for (int jp = 0; jp < BM / 2; ++jp) {
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (2 * jp < Bb) q = row4[jp];
+        const float2 c0 = pcr[2 * jp], c1 = pcr[2 * jp + 1];
+        v[2 * jp] = make_float2(fmaf(q.x, c0.x, -q.y * c0.y), fmaf(q.x, c0.y, q.y * c0.x));
+        v[2 * jp + 1] = make_float2(fmaf(q.z, c1.x, -q.w * c1.y), fmaf(q.z, c1.y, q.w * c1.x));
+      }
+      if (!is_tail)
+        apply_w<BM>(W.w, v, acc);
+      else
+        apply_w<BM>(W.wt, v, acc);
+#pragma unroll
+      for (int jp = 0; jp < BM / 2; ++jp)
+        if (2 * jp < Bb) row4[jp] = make_float4(acc[2 * jp].x, acc[2 * jp].y, acc[2 * jp + 1].x, acc[2 * jp + 1].y);
+    }
+    fence_proxy_async_shared();
+    __syncthreads();
+    if (*s_abort) {
+      if (tid == 0) {
+        bulk_wait_all();
+        atomicExch(status, int(RAPRO_ERR_TIMEOUT));
+      }
+      return;
+    }
+    if (tid == 0) {
+      bulk_store(out + (row0 + r) * N, row, row_bytes);
+      bulk_commit();
+      const int rn = r + STREAM_BUF;
+      if (rn < nrows) {
+        bulk_wait_read<0>();                 // the store of this buffer has read it
+        mbar_arrive_expect_tx(&bars[1 + slot], row_bytes);
+        bulk_load(row, y + (row0 + rn) * N, row_bytes, &bars[1 + slot]);
       }
     }
   }
-  float2 acc[BM];
-  if (!is_tail)
-    apply_w<BM>(W.w, v, acc);
-  else
-    apply_w<BM>(W.wt, v, acc);
-#pragma unroll
-  for (int i = 0; i < BM; ++i)
-    if (i < Bb) out[base + i] = acc[i];
+  if (tid == 0) bulk_wait_all();
+}
+
+size_t lmmse_stream_smem(int N) { return 128 + size_t(N) * sizeof(float2) * (1 + STREAM_BUF); }
+
+template <int BM>
+static void fill_small(WSmall<BM>& W, const float2* w_main, const float2* w_tail, int B, int tail) {
+  for (int i = 0; i < BM * BM; ++i) W.w[i] = W.wt[i] = make_float2(0.f, 0.f);
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) W.w[i * BM + j] = w_main[size_t(i) * B + j];
+  for (int i = 0; i < tail; ++i)
+    for (int j = 0; j < tail; ++j) W.wt[i * BM + j] = w_tail[size_t(i) * tail + j];
+}
+
+static bool stream_ok(const float2* y, const float2* pil, const float2* out, int N, int B, int nb) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(pil) |
+                      reinterpret_cast<uintptr_t>(out);
+  return (a & 15) == 0 && N % 2 == 0 && B % 2 == 0 && nb <= STREAM_MAX_THREADS &&
+         lmmse_stream_smem(N) <= size_t(200) * 1024;
+}
+
+template <int BM>
+static cudaError_t launch_stream(const WSmall<BM>& W, const float2* y, const float2* pil, float2* out,
+                                 int T, int K, int M, int N, int B, int nb, int tail, int* status,
+                                 cudaStream_t st) {
+  const size_t smem = lmmse_stream_smem(N);
+  dim3 grid((M + STREAM_ROWS - 1) / STREAM_ROWS, T * K);
+  const int threads = std::max(32, (nb + 31) / 32 * 32);
+  lmmse_stream_kernel<BM><<<grid, threads, smem, st>>>(y, pil, out, M, N, B, nb, tail, status, W);
+  return cudaGetLastError();
 }
 
 template <int BM>
 static cudaError_t launch_small(const Plan& pl, const float2* x, const float2* pil, float2* out,
                                 cudaStream_t st) {
   WSmall<BM> W;
-  for (int i = 0; i < BM * BM; ++i) W.w[i] = W.wt[i] = make_float2(0.f, 0.f);
-  for (int i = 0; i < pl.B; ++i)
-    for (int j = 0; j < pl.B; ++j) W.w[i * BM + j] = pl.w_main[size_t(i) * pl.B + j];
-  for (int i = 0; i < pl.tail; ++i)
-    for (int j = 0; j < pl.tail; ++j) W.wt[i * BM + j] = pl.w_tail[size_t(i) * pl.tail + j];
+  fill_small<BM>(W, pl.w_main.data(), pl.w_tail.data(), pl.B, pl.tail);
+  if (pil && stream_ok(x, pil, out, pl.p.n_sc, pl.B, pl.nb))
+    return launch_stream<BM>(W, x, pil, out, pl.T, pl.p.K, pl.p.M, pl.p.n_sc, pl.B, pl.nb, pl.tail,
+                             pl.d_status, st);
   const int rows = pl.T * pl.p.K * pl.p.M;
-  dim3 grid((rows + 127) / 128, pl.nb);
+  dim3 grid((pl.nb + SEG_BLOCKS - 1) / SEG_BLOCKS, rows);
   if (pil)
-    lmmse_small_kernel<BM, true><<<grid, 128, 0, st>>>(x, pil, out, rows, pl.p.M, pl.p.n_sc, pl.B,
-                                                      pl.nb, pl.tail, W);
+    lmmse_small_kernel<BM, true><<<grid, SMALL_THREADS, 0, st>>>(x, pil, out, pl.p.M, pl.p.n_sc, pl.B,
+                                                                pl.nb, pl.tail, W);
   else
-    lmmse_small_kernel<BM, false><<<grid, 128, 0, st>>>(x, pil, out, rows, pl.p.M, pl.p.n_sc, pl.B,
-                                                       pl.nb, pl.tail, W);
+    lmmse_small_kernel<BM, false><<<grid, SMALL_THREADS, 0, st>>>(x, pil, out, pl.p.M, pl.p.n_sc, pl.B,
+                                                                 pl.nb, pl.tail, W);
   return cudaGetLastError();
 }
 
@@ -209,29 +373,47 @@ static cudaError_t launch_tiled(const Plan& pl, const float2* x, const float2* p
 template <int BM>
 static cudaError_t launch_small_raw(const float2* w_main, const float2* w_tail, int B, int tail,
                                     int nb, int rows, int M, int N, const float2* y,
-                                    const float2* pil, float2* out, cudaStream_t st) {
+                                    const float2* pil, float2* out, int* status, cudaStream_t st) {
   WSmall<BM> W;
-  for (int i = 0; i < BM * BM; ++i) W.w[i] = W.wt[i] = make_float2(0.f, 0.f);
-  for (int i = 0; i < B; ++i)
-    for (int j = 0; j < B; ++j) W.w[i * BM + j] = w_main[i * B + j];
-  for (int i = 0; i < tail; ++i)
-    for (int j = 0; j < tail; ++j) W.wt[i * BM + j] = w_tail[i * tail + j];
-  dim3 grid((rows + 127) / 128, nb);
-  lmmse_small_kernel<BM, true><<<grid, 128, 0, st>>>(y, pil, out, rows, M, N, B, nb, tail, W);
+  fill_small<BM>(W, w_main, w_tail, B, tail);
+  if (status && stream_ok(y, pil, out, N, B, nb))
+    return launch_stream<BM>(W, y, pil, out, 1, rows / M, M, N, B, nb, tail, status, st);
+  dim3 grid((nb + SEG_BLOCKS - 1) / SEG_BLOCKS, rows);
+  lmmse_small_kernel<BM, true><<<grid, SMALL_THREADS, 0, st>>>(y, pil, out, M, N, B, nb, tail, W);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ls_lmmse_small_raw(const float2* w_main, const float2* w_tail, int B, int tail,
                                       int nb, int rows, int M, int N, const float2* y,
-                                      const float2* pil, float2* out, cudaStream_t st) {
-  if (B <= 4) return launch_small_raw<4>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
-  if (B <= 8) return launch_small_raw<8>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
-  if (B <= 12) return launch_small_raw<12>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
-  if (B <= 16) return launch_small_raw<16>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
-  if (B <= 24) return launch_small_raw<24>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+                                      const float2* pil, float2* out, int* status, cudaStream_t st) {
+  if (B <= 4) return launch_small_raw<4>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, status, st);
+  if (B <= 8) return launch_small_raw<8>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, status, st);
+  if (B <= 12) return launch_small_raw<12>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, status, st);
+  if (B <= 16) return launch_small_raw<16>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, status, st);
+  if (B <= 24) return launch_small_raw<24>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, status, st);
   if (B <= LMMSE_SMALL_MAX)
-    return launch_small_raw<32>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, st);
+    return launch_small_raw<32>(w_main, w_tail, B, tail, nb, rows, M, N, y, pil, out, status, st);
   return cudaErrorInvalidValue;
+}
+
+// Raise the streaming kernels' dynamic shared-memory limit once per device, at plan
+// creation (not at launch, which may be inside a CUDA-graph capture).
+cudaError_t prepare_estimate(int device) {
+  static std::once_flag flags[64];
+  static cudaError_t result[64];
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  std::call_once(flags[device], [device] {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int lim = 200 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(lmmse_stream_kernel<4>, A, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_stream_kernel<8>, A, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_stream_kernel<12>, A, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_stream_kernel<16>, A, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_stream_kernel<24>, A, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_stream_kernel<32>, A, lim);
+    result[device] = e;
+  });
+  return result[device];
 }
 
 cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,

@@ -65,6 +65,7 @@ cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
                          cudaStream_t st);
 
 cudaError_t prepare_detect(int device);
+cudaError_t prepare_estimate(int device);
 
 cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
                           unsigned char* labels, float* llr, int* info, cudaStream_t st);
@@ -72,7 +73,7 @@ cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, floa
 // Plan-free launchers used by the allocation-free receive entry point.
 cudaError_t launch_ls_lmmse_small_raw(const float2* w_main, const float2* w_tail, int B, int tail,
                                       int nb, int rows, int M, int N, const float2* y,
-                                      const float2* pil, float2* out, cudaStream_t st);
+                                      const float2* pil, float2* out, int* status, cudaStream_t st);
 cudaError_t launch_detect_raw(const DetTiles& tiles, int T, int K, int M, int N, int D, int q,
                               float sigma2, int* status, const float2* h, const float2* y,
                               float2* x_eq, unsigned char* labels, float* llr, int* info,

@@ -37,13 +37,14 @@ DeviceScratch g_scratch[kMaxDevices];
 std::once_flag g_once[kMaxDevices];
 
 // Once per device, with that device current: the device addresses of the arrays (their
-// names are host-side stand-ins in host code) and the detector's shared-memory limit.
+// names are host-side stand-ins in host code) and the kernels' shared-memory limits.
 const DeviceScratch& device_scratch(int dev) {
   std::call_once(g_once[dev], [dev] {
     DeviceScratch& s = g_scratch[dev];
     s.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.h), g_noalloc_h);
     if (s.err == cudaSuccess) s.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.status), g_noalloc_status);
     if (s.err == cudaSuccess) s.err = prepare_detect(dev);
+    if (s.err == cudaSuccess) s.err = prepare_estimate(dev);
   });
   return g_scratch[dev];
 }
@@ -157,7 +158,7 @@ extern "C" rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, co
   const float2* yp = reinterpret_cast<const float2*>(y_pilot);
   const float2* pil = reinterpret_cast<const float2*>(pilots);
   e = launch_ls_lmmse_small_raw(w_main, w_tail, B, tail, nb, T * p->K * p->M, p->M, p->n_sc, yp, pil,
-                                ds.h, st);
+                                ds.h, ds.status, st);
   if (e != cudaSuccess) return cuda_fail(e, "LS+LMMSE kernel launch");
   const DetTiles tiles = make_det_tiles(p->K, D);
   e = launch_detect_raw(tiles, T, p->K, p->M, p->n_sc, D, p->qam_bits, float(p->sigma2), ds.status, ds.h,

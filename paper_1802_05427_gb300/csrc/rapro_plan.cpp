@@ -228,6 +228,7 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   cudaError_t e = cudaGetDevice(&pl->device);
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDevice"); }
   if ((e = prepare_detect(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "detector set-up"); }
+  if ((e = prepare_estimate(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "estimator set-up"); }
   const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
