@@ -4,16 +4,19 @@
 // One CTA owns DET_SC = 16 consecutive subcarriers of one slot.  The channel estimate
 // h[t][s][m][k] and the slot's data symbols y[t*D+n][m][k] stream through shared memory
 // DET_MCH = 8 antennas at a time as TMA boxes (16 subcarriers x 8 antennas x K users, and
-// x D symbols) in a DET_STAGES-deep mbarrier pipeline.  Each warp owns one 4 x 6 tile of
-// the augmented product: rows are users i, columns are users j (Gram entries
-// A[i][j] = sum_m conj(h_i) h_j) or data symbols n (matched filter z[i][n] =
-// sum_m conj(h_i) y_n); lanes 0-15 and 16-31 take the two antenna halves of a chunk.
+// x D symbols) in a DET_STAGES-deep mbarrier pipeline.  Each warp owns one role (see
+// DetTiles): the lower triangle of a 4-user Gram block plus one off-diagonal block, or a
+// 4-user x 6-symbol matched-filter block, so every entry of A[i][j] = sum_m conj(h_i) h_j
+// (j <= i) and z[i][n] = sum_m conj(h_i) y_n is computed once.  Lane = subcarrier; the
+// antennas of a chunk are split between the two half-warps and, when there are few roles,
+// between two warps per role.  A producer warp issues the TMA loads; consumer warps free a
+// stage through an mbarrier, so no CTA-wide barrier sits in the antenna loop.
 //
-// Epilogue, one half-warp per subcarrier, lane i holding row i in registers:
-//   Cholesky of A + sigma2 I by columns (pivot and column broadcast by shuffles),
-//   w = L^-1 z (forward substitution, lane-per-row), the rows of L^-1 (same scheme with
-//   the identity), s_k = sigma2 [A^-1]_kk = sigma2 sum_i |[L^-1]_ik|^2 (butterfly column
-//   sums), x~ = L^-H w from the rows of L^-1 and w exchanged through shared memory.
+// Epilogue, one half-warp per subcarrier:
+//   Cholesky of A + sigma2 I by columns, lane i holding row i (pivot and column broadcast
+//   by shuffles); L to shared memory; lane i computes column i of L^-1 by forward
+//   substitution (L reads broadcast) and s_i = sigma2 [A^-1]_ii = sigma2 sum_j |L^-1[j][i]|^2;
+//   w = L^-1 z lane-per-row and x~ = L^-H w lane-per-column, through shared memory.
 // Then all threads demap (x^ = x~ / mu, mu = 1 - s) and store with coalesced writes.
 #pragma once
 
@@ -52,18 +55,28 @@ __host__ __device__ constexpr size_t det_epilogue_bytes(int KT, int DT) {
          size_t(DET_SC) * 4;
 }
 
-// Threads of the largest tile set of a (KT, DT) class: the tile count of make_det_tiles
-// at K = KT, D = DT (one warp per tile).
+// Threads of the largest role set of a (KT, DT) class (make_det_tiles at K = KT, D = DT):
+// NG triangle roles, the off-diagonal blocks left after pairing one with each triangle,
+// NG x data-group blocks; two warps per role when there are at most 8 roles.
 __host__ __device__ constexpr int det_max_threads(int KT, int DT) {
-  int n = 0;
-  for (int a = 0; a < (KT + 3) / 4; ++a)
-    for (int c = 0; c < (KT + 5) / 6; ++c)
-      if (6 * c <= 4 * a + 3) ++n;
-  return 32 * (n + ((KT + 3) / 4) * ((DT + 5) / 6));
+  const int ng = (KT + 3) / 4, nr = ng * (ng - 1) / 2, ndg = (DT + 5) / 6;
+  const int roles = ng + (nr > ng ? nr - ng : 0) + ng * ndg;
+  const int warps = roles * (roles <= 8 ? 2 : 1) + 1;       // + the TMA producer warp
+  return 32 * (warps < DET_SC / 2 ? DET_SC / 2 : warps);     // at least one warp per 2 subcarriers
+}
+
+inline int det_block_threads(const DetTiles& t) {
+  const int warps = t.n_roles * t.msplit + 1;
+  return 32 * (warps < DET_SC / 2 ? DET_SC / 2 : warps);
+}
+
+// Partial sums of the second warp of each role, parked for the first (after A/z).
+__host__ __device__ constexpr size_t det_scratch_bytes(int KT, int DT) {
+  return size_t(det_max_threads(KT, DT) / 32) * 16 * 26 * 8;
 }
 
 inline size_t det_stage_bytes(const DetTiles& t) {
-  return size_t(t.KP6 + t.DP6) * DET_MCH * DET_SC * sizeof(float2);
+  return size_t(t.KP + t.DP) * DET_MCH * DET_SC * sizeof(float2);
 }
 
 // --------------------------------------------------------------- demapper helpers
@@ -102,7 +115,7 @@ __device__ __forceinline__ void demap_store(float2 xt, float s, size_t o, unsign
   constexpr int Q = 2 * MB;
   const float scale = (MB == 1) ? 1.41421356237309505f : (MB == 2 ? 3.16227766016837933f : 6.48074069840786023f);
   const float mu = 1.0f - s;
-  const float inv_mu = 1.0f / mu;
+  const float inv_mu = __fdividef(1.0f, mu);
   const float nu = s * inv_mu;
   float ddI[MB], ddQ[MB];
   const int gI = pam_demap<MB>(xt.x * inv_mu * scale, ddI);
@@ -117,7 +130,7 @@ __device__ __forceinline__ void demap_store(float2 xt, float s, size_t o, unsign
     labels[o] = (unsigned char)lab;
   }
   if (llr) {
-    const float g = 1.0f / (nu * scale * scale);
+    const float g = __fdividef(1.0f, nu * scale * scale);
 #pragma unroll
     for (int p = 0; p < MB; ++p) {
       llr[o * Q + 2 * p] = ddI[p] * g;
@@ -142,127 +155,208 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   const int nwarps = blockDim.x >> 5;
   const int t = blockIdx.y, k0 = blockIdx.x * DET_SC;
   const int K = P.K, D = P.D, M = P.M, N = P.N;
-  const int KP6 = P.tiles.KP6, DP6 = P.tiles.DP6;
-  const int stage_elems = (KP6 + DP6) * DET_MCH * DET_SC;
+  const int KP = P.tiles.KP, DP = P.tiles.DP;
+  const int stage_elems = (KP + DP) * DET_MCH * DET_SC;
   const int nst = USE_TMA ? DET_STAGES : 1;
 
-  // Zero the padding rows (users K..KP6-1, symbols D..DP6-1) of every stage once; the
+  // Zero the padding rows (users K..KP-1, symbols D..DP-1) of every stage once; the
   // loads never write them.
   for (int s = 0; s < nst; ++s) {
     float2* st = stage0 + s * stage_elems;
-    for (int e = threadIdx.x; e < (KP6 - K) * DET_MCH * DET_SC; e += blockDim.x)
+    for (int e = threadIdx.x; e < (KP - K) * DET_MCH * DET_SC; e += blockDim.x)
       st[K * DET_MCH * DET_SC + e] = make_float2(0.f, 0.f);
-    for (int e = threadIdx.x; e < (DP6 - D) * DET_MCH * DET_SC; e += blockDim.x)
-      st[(KP6 + D) * DET_MCH * DET_SC + e] = make_float2(0.f, 0.f);
+    for (int e = threadIdx.x; e < (DP - D) * DET_MCH * DET_SC; e += blockDim.x)
+      st[(KP + D) * DET_MCH * DET_SC + e] = make_float2(0.f, 0.f);
   }
+  // Consumer warps (one or two per role) and, on the TMA path, one producer warp (the last).
+  const int n_cons = P.tiles.n_roles * P.tiles.msplit;
+  uint64_t* full = bars;                      // [DET_STAGES] TMA bytes landed
+  uint64_t* empty = bars + DET_STAGES;        // [DET_STAGES] every consumer warp is done
   if (threadIdx.x == 0) {
     *s_abort = 0;
     if (USE_TMA) {
-      for (int s = 0; s < DET_STAGES; ++s) mbar_init(&bars[s], 1);
+      for (int s = 0; s < DET_STAGES; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], n_cons);
+      }
       fence_mbar_init();
     }
   }
   __syncthreads();
 
   const uint32_t stage_tx = uint32_t((K + D) * DET_MCH * DET_SC * sizeof(float2));
-  auto issue = [&](int c, int s) {
-    float2* st = stage0 + s * stage_elems;
-    mbar_arrive_expect_tx(&bars[s], stage_tx);
-    tma_load_3d(st, &map_h, &bars[s], k0, c * DET_MCH, t * K);
-    tma_load_3d(st + KP6 * DET_MCH * DET_SC, &map_y, &bars[s], k0, c * DET_MCH, t * D);
-  };
-  if (USE_TMA && threadIdx.x == 0) {
-    prefetch_tensormap(&map_h);
-    prefetch_tensormap(&map_y);
-    for (int c = 0; c < DET_STAGES && c < P.nchunks; ++c) issue(c, c);
+  if (USE_TMA && warp == n_cons) {
+    // Producer: stream every antenna chunk through the stage ring.
+    if (lane == 0) {
+      prefetch_tensormap(&map_h);
+      prefetch_tensormap(&map_y);
+      for (int c = 0; c < P.nchunks; ++c) {
+        const int s = c % DET_STAGES;
+        if (c >= DET_STAGES && !mbar_wait_bounded(&empty[s], uint32_t(c / DET_STAGES - 1) & 1u)) {
+          atomicExch(s_abort, 1);
+          break;
+        }
+        float2* st = stage0 + s * stage_elems;
+        mbar_arrive_expect_tx(&full[s], stage_tx);
+        tma_load_3d(st, &map_h, &full[s], k0, c * DET_MCH, t * K);
+        tma_load_3d(st + KP * DET_MCH * DET_SC, &map_y, &full[s], k0, c * DET_MCH, t * D);
+      }
+    }
+    __syncwarp();
   }
 
   // ------------------------------------------------ accumulation: Gram and z
-  const int a = P.tiles.row_group[warp], coff = P.tiles.col_off[warp];
+  const int R = P.tiles.n_roles;
+  const int role = warp % R, mg = warp / R;
+  const int kind = P.tiles.kind[role], rg = P.tiles.g[role], rr = P.tiles.r[role], rc = P.tiles.c[role];
   const int sc = lane & 15, mh = lane >> 4;
-  float2 acc[4][6];
+  const int per = DET_MCH / (2 * P.tiles.msplit);      // antennas of a chunk per half-warp
+  const int m_first = (mg * 2 + mh) * per;
+  constexpr int PL = DET_MCH * DET_SC;                 // one operand row of a stage
+  float2 acc[26];
 #pragma unroll
-  for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-    for (int jj = 0; jj < 6; ++jj) acc[ii][jj] = make_float2(0.f, 0.f);
+  for (int e = 0; e < 26; ++e) acc[e] = make_float2(0.f, 0.f);
 
+  const bool consumer = warp < n_cons;
   for (int c = 0; c < P.nchunks; ++c) {
     const int s = USE_TMA ? (c % DET_STAGES) : 0;
     float2* st = stage0 + s * stage_elems;
     if (USE_TMA) {
-      if (!mbar_wait_bounded(&bars[s], uint32_t(c / DET_STAGES) & 1u)) atomicExch(s_abort, 1);
+      if (!consumer) break;
+      if (!mbar_wait_bounded(&full[s], uint32_t(c / DET_STAGES) & 1u)) {
+        atomicExch(s_abort, 1);
+        break;
+      }
     } else {
-      // Plain loads with bounds checks (odd n_sc or unaligned pointers).
+      // Plain loads with bounds checks (odd n_sc or unaligned pointers), all threads.
       const int m0 = c * DET_MCH;
-      for (int e = threadIdx.x; e < (K + D) * DET_MCH * DET_SC; e += blockDim.x) {
-        const int op = e / (DET_MCH * DET_SC), rem = e % (DET_MCH * DET_SC);
+      for (int e = threadIdx.x; e < (K + D) * PL; e += blockDim.x) {
+        const int op = e / PL, rem = e % PL;
         const int m = m0 + rem / DET_SC, k = k0 + rem % DET_SC;
         float2 v = make_float2(0.f, 0.f);
         if (m < M && k < N)
           v = (op < K) ? h[(size_t(t * K + op) * M + m) * N + k] : y[(size_t(t * D + op - K) * M + m) * N + k];
-        const int dst = (op < K) ? op : KP6 + (op - K);
-        st[dst * DET_MCH * DET_SC + rem] = v;
+        const int dst = (op < K) ? op : KP + (op - K);
+        st[dst * PL + rem] = v;
       }
       __syncthreads();
     }
+    if (consumer) {
+      const float2* sl = st + sc;
 #pragma unroll
-    for (int mm = 0; mm < DET_MCH / 2; ++mm) {
-      const int m = mh * (DET_MCH / 2) + mm;
-      float2 r[4], cv[6];
+      for (int mm = 0; mm < DET_MCH / 2; ++mm) {
+        if (mm < per) {
+          const int mo = (m_first + mm) * DET_SC;
+          if (kind == 2) {
+            float2 a4[4], y6[6];
 #pragma unroll
-      for (int ii = 0; ii < 4; ++ii) r[ii] = st[((4 * a + ii) * DET_MCH + m) * DET_SC + sc];
+            for (int ii = 0; ii < 4; ++ii) a4[ii] = sl[(4 * rg + ii) * PL + mo];
 #pragma unroll
-      for (int jj = 0; jj < 6; ++jj) cv[jj] = st[((coff + jj) * DET_MCH + m) * DET_SC + sc];
+            for (int jj = 0; jj < 6; ++jj) y6[jj] = sl[(KP + 6 * rc + jj) * PL + mo];
 #pragma unroll
-      for (int ii = 0; ii < 4; ++ii)
+            for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 6; ++jj) cmac_conj(acc[ii][jj], r[ii], cv[jj]);
-    }
-    __syncthreads();
-    if (*s_abort) {
-      // A pipeline wait ran out: give the copies in flight a bounded chance to land,
-      // record the timeout and leave without touching the outputs.
-      if (threadIdx.x == 0) {
-        for (int cc = c; cc < P.nchunks && cc < c + DET_STAGES; ++cc)
-          (void)mbar_wait_bounded(&bars[cc % DET_STAGES], uint32_t(cc / DET_STAGES) & 1u);
-        atomicExch(P.status, int(RAPRO_ERR_TIMEOUT));
+              for (int jj = 0; jj < 6; ++jj) cmac_conj(acc[ii * 6 + jj], a4[ii], y6[jj]);
+          } else {
+            if (kind == 0) {
+              float2 t4[4];
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii) t4[ii] = sl[(4 * rg + ii) * PL + mo];
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj <= ii; ++jj) cmac_conj(acc[ii * (ii + 1) / 2 + jj], t4[ii], t4[jj]);
+            }
+            if (rr >= 0) {
+              float2 r4[4], c4[4];
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii) r4[ii] = sl[(4 * rr + ii) * PL + mo];
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) c4[jj] = sl[(4 * rc + jj) * PL + mo];
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) cmac_conj(acc[10 + ii * 4 + jj], r4[ii], c4[jj]);
+            }
+          }
+        }
       }
-      return;
     }
-    if (USE_TMA && threadIdx.x == 0 && c + DET_STAGES < P.nchunks) issue(c + DET_STAGES, s);
+    if (USE_TMA) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);          // this warp is done with the stage
+    } else {
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (*s_abort) {
+    // A pipeline wait ran out: give the copies in flight a bounded chance to land,
+    // record the timeout and leave without touching the outputs.
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < DET_STAGES; ++s) (void)mbar_wait_bounded(&full[s], 0);
+      atomicExch(P.status, int(RAPRO_ERR_TIMEOUT));
+    }
+    return;
   }
 
+  // Sum the antenna halves (lanes) and, with two warps per role, the two warps.
 #pragma unroll
-  for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-    for (int jj = 0; jj < 6; ++jj) {
-      acc[ii][jj].x += __shfl_xor_sync(0xffffffffu, acc[ii][jj].x, 16);
-      acc[ii][jj].y += __shfl_xor_sync(0xffffffffu, acc[ii][jj].y, 16);
-    }
-
-  // The stages are free: A (+ sigma2 I) and z go to shared memory.
+  for (int e = 0; e < 26; ++e) {
+    acc[e].x += __shfl_xor_sync(0xffffffffu, acc[e].x, 16);
+    acc[e].y += __shfl_xor_sync(0xffffffffu, acc[e].y, 16);
+  }
   constexpr int AS = KT + 1;                                    // padded row stride
   float2* As = stage0;                                          // [DET_SC][KT][AS], later rows of L^-1
   float2* Zs = As + DET_SC * KT * AS;                           // [DET_SC][KT][DT], later w, then x~ [n][k]
   float* Ss = reinterpret_cast<float*>(Zs + DET_SC * KT * DT);  // [DET_SC][KT]  s_k
   int* Is = reinterpret_cast<int*>(Ss + DET_SC * KT);           // [DET_SC]      info
-  if (mh == 0) {
+  float2* park = reinterpret_cast<float2*>(stage0) + det_epilogue_bytes(KT, DT) / sizeof(float2);
+  if (P.tiles.msplit == 2) {
+    if (mg == 1 && mh == 0) {
 #pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      const int i = 4 * a + ii;
-      if (i >= K) continue;
+      for (int e = 0; e < 26; ++e) park[(role * 16 + sc) * 26 + e] = acc[e];
+    }
+    __syncthreads();
+    if (mg == 0 && mh == 0) {
 #pragma unroll
-      for (int jj = 0; jj < 6; ++jj) {
-        const int col = coff + jj;
-        if (col < KP6) {
-          if (col < K) {
-            float2 v = acc[ii][jj];
-            if (col == i) v.x += P.sigma2;
-            As[(sc * KT + i) * AS + col] = v;
-          }
-        } else if (col - KP6 < D) {
-          Zs[(sc * KT + i) * DT + (col - KP6)] = acc[ii][jj];
+      for (int e = 0; e < 26; ++e) {
+        const float2 o = park[(role * 16 + sc) * 26 + e];
+        acc[e].x += o.x;
+        acc[e].y += o.y;
+      }
+    }
+  }
+  // A (+ sigma2 I, lower triangle) and z to shared memory.
+  if (mg == 0 && mh == 0) {
+    if (kind == 2) {
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 6; ++jj) {
+          const int i = 4 * rg + ii, n = 6 * rc + jj;
+          if (i < K && n < D) Zs[(sc * KT + i) * DT + n] = acc[ii * 6 + jj];
         }
+    } else {
+      if (kind == 0) {
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int jj = 0; jj <= ii; ++jj) {
+            const int i = 4 * rg + ii, j = 4 * rg + jj;
+            float2 v = acc[ii * (ii + 1) / 2 + jj];
+            if (ii == jj) v.x += P.sigma2;
+            if (i < K) As[(sc * KT + i) * AS + j] = v;
+          }
+      }
+      if (rr >= 0) {
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int i = 4 * rr + ii, j = 4 * rc + jj;
+            if (i < K && j < K) As[(sc * KT + i) * AS + j] = acc[10 + ii * 4 + jj];
+          }
       }
     }
   }
@@ -271,19 +365,21 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   // --------------------------------------------- factorisation and solves
   const int hw = lane >> 4, i = lane & 15, base = hw << 4;
   const unsigned FULL = 0xffffffffu;
-  for (int scl = warp * 2 + hw; scl < DET_SC; scl += 2 * nwarps) {
+  // Every CTA has at least DET_SC / 2 warps, so each half-warp takes at most one subcarrier
+  // (a single pass keeps the row arrays in registers).
+  const int scl = warp * 2 + hw;
+  if (scl < DET_SC) {
     const bool live = i < K;                 // real user row
-    float2 ar[KT], zr[DT];
+    float2* Am = As + scl * KT * AS;         // this subcarrier: A, then L, then L^-1 (by columns)
+    float2* Zm = Zs + scl * KT * DT;         // z, then w, then x~ as [n][k]
+    float2 ar[KT];
 #pragma unroll
     for (int j = 0; j < KT; ++j) {
-      if (live && j <= i) ar[j] = As[(scl * KT + i) * AS + j];
+      if (live && j <= i) ar[j] = Am[i * AS + j];
       else ar[j] = make_float2((i < KT && j == i) ? 1.f : 0.f, 0.f);   // padded rows: identity
     }
-#pragma unroll
-    for (int n = 0; n < DT; ++n) zr[n] = (live && n < D) ? Zs[(scl * KT + i) * DT + n] : make_float2(0.f, 0.f);
-    __syncwarp();
 
-    // Cholesky, column j at a time: every lane reads the pivot, so each knows L_jj.
+    // Cholesky, column j at a time; every lane reads the pivot, so each knows 1 / L_jj.
     float inv_l[KT];
     int fail = 0;
 #pragma unroll
@@ -291,10 +387,9 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
       const float d = __shfl_sync(FULL, ar[j].x, base + j);
       const bool ok = (d > 0.0f) && (d < 3.0e38f);
       if (!ok && fail == 0) fail = j + 1;
-      const float lj = sqrtf(d);
-      const float il = 1.0f / lj;
+      const float il = rsqrtf(d);                            // 1 / L_jj
       inv_l[j] = il;
-      if (i == j) ar[j] = make_float2(lj, 0.f);
+      if (i == j) ar[j] = make_float2(d * il, 0.f);
       else if (i > j) ar[j] = make_float2(ar[j].x * il, ar[j].y * il);
 #pragma unroll
       for (int l = j + 1; l < KT; ++l) {
@@ -307,74 +402,64 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
         }
       }
     }
-    // w = L^-1 z, lane i ends with w_i.
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-#pragma unroll
-      for (int n = 0; n < DT; ++n) {
-        float2 wj;
-        wj.x = __shfl_sync(FULL, zr[n].x, base + j) * inv_l[j];
-        wj.y = __shfl_sync(FULL, zr[n].y, base + j) * inv_l[j];
-        if (i == j) zr[n] = wj;
-        else if (i > j) {
-          zr[n].x -= fmaf(ar[j].x, wj.x, -ar[j].y * wj.y);
-          zr[n].y -= fmaf(ar[j].x, wj.y, ar[j].y * wj.x);
-        }
-      }
-    }
-    // Rows of L^-1 (forward substitution of the identity), lane i ends with row i.
-    float2 yr[KT];
-#pragma unroll
-    for (int k = 0; k < KT; ++k) yr[k] = make_float2(k == i ? 1.f : 0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-#pragma unroll
-      for (int k = 0; k <= j; ++k) {
-        float2 yj;
-        yj.x = __shfl_sync(FULL, yr[k].x, base + j) * inv_l[j];
-        yj.y = __shfl_sync(FULL, yr[k].y, base + j) * inv_l[j];
-        if (i == j) yr[k] = yj;
-        else if (i > j) {
-          yr[k].x -= fmaf(ar[j].x, yj.x, -ar[j].y * yj.y);
-          yr[k].y -= fmaf(ar[j].x, yj.y, ar[j].y * yj.x);
-        }
-      }
-    }
-    // s_k = sigma2 sum_i |[L^-1]_ik|^2 over the real user rows.
-    float sq[KT];
-#pragma unroll
-    for (int k = 0; k < KT; ++k) sq[k] = live ? fmaf(yr[k].x, yr[k].x, yr[k].y * yr[k].y) : 0.f;
-#pragma unroll
-    for (int off = 8; off >= 1; off >>= 1)
-#pragma unroll
-      for (int k = 0; k < KT; ++k) sq[k] += __shfl_xor_sync(FULL, sq[k], off);
-    // Exchange rows of L^-1 and w through shared memory for x~ = L^-H w.
+    __syncwarp();
     if (i < KT) {
 #pragma unroll
-      for (int k = 0; k < KT; ++k) As[(scl * KT + i) * AS + k] = yr[k];
-#pragma unroll
-      for (int n = 0; n < DT; ++n) Zs[(scl * KT + i) * DT + n] = zr[n];
+      for (int j = 0; j < KT; ++j) Am[i * AS + j] = ar[j];   // row i of L (zero above the diagonal)
     }
-    if (live) {
-      float sk = 0.f;
+    __syncwarp();
+    // Column i of L^-1: y_i = 1 / L_ii, y_j = -(sum_{i <= l < j} L[j][l] y_l) / L_jj (j > i);
+    // the L[j][l] reads are the same address across lanes (broadcast).
+    float2 yc[KT];
+    float sk = 0.f;
 #pragma unroll
-      for (int k = 0; k < KT; ++k)
-        if (k == i) sk = sq[k];
-      Ss[scl * KT + i] = P.sigma2 * sk;
+    for (int j = 0; j < KT; ++j) {
+      float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int l = 0; l < j; ++l) cmac(acc2, Am[j * AS + l], yc[l]);   // yc[l] = 0 for l < i
+      const float il = inv_l[j];
+      yc[j] = (j == i) ? make_float2(il, 0.f) : ((j > i) ? make_float2(-acc2.x * il, -acc2.y * il)
+                                                           : make_float2(0.f, 0.f));
+      sk = fmaf(yc[j].x, yc[j].x, fmaf(yc[j].y, yc[j].y, sk));
     }
+    __syncwarp();
+    if (i < KT) {
+#pragma unroll
+      for (int j = 0; j < KT; ++j) Am[j * AS + i] = yc[j];   // L^-1[j][i]
+    }
+    if (live) Ss[scl * KT + i] = P.sigma2 * sk;
     if (i == 0) Is[scl] = fail;
     __syncwarp();
-    float2 xk[DT];
+    // w_i = sum_{l <= i} L^-1[i][l] z_l  (row i of L^-1; the z reads broadcast).
+    float2 wr[DT];
 #pragma unroll
-    for (int n = 0; n < DT; ++n) xk[n] = make_float2(0.f, 0.f);
+    for (int n = 0; n < DT; ++n) wr[n] = make_float2(0.f, 0.f);
     if (live) {
-      for (int r = i; r < K; ++r) {
-        const float2 Y = As[(scl * KT + r) * AS + i];        // [L^-1]_{r,i}, use its conjugate
 #pragma unroll
-        for (int n = 0; n < DT; ++n) {
-          const float2 w = Zs[(scl * KT + r) * DT + n];
-          xk[n].x = fmaf(Y.x, w.x, fmaf(Y.y, w.y, xk[n].x));
-          xk[n].y = fmaf(Y.x, w.y, fmaf(-Y.y, w.x, xk[n].y));
+      for (int l = 0; l < KT; ++l) {
+        if (l < K) {
+          const float2 Y = Am[i * AS + l];
+#pragma unroll
+          for (int n = 0; n < DT; ++n) cmac(wr[n], Y, Zm[l * DT + n]);
+        }
+      }
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int n = 0; n < DT; ++n) Zm[i * DT + n] = wr[n];
+    }
+    __syncwarp();
+    // x~_i = sum_{j >= i} conj(L^-1[j][i]) w_j  (column i of L^-1 is still in yc).
+    float2 xr[DT];
+#pragma unroll
+    for (int n = 0; n < DT; ++n) xr[n] = make_float2(0.f, 0.f);
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < KT; ++j) {
+        if (j < K) {
+#pragma unroll
+          for (int n = 0; n < DT; ++n) cmac_conj(xr[n], yc[j], Zm[j * DT + n]);
         }
       }
     }
@@ -382,7 +467,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     if (live) {
 #pragma unroll
       for (int n = 0; n < DT; ++n)
-        if (n < D) Zs[(scl * DT + n) * KT + i] = xk[n];       // x~ as [sc][n][k]
+        if (n < D) Zm[n * KT + i] = xr[n];                   // x~ as [n][k]
     }
     __syncwarp();
   }
@@ -430,7 +515,7 @@ template <> cudaError_t detect_prepare_kt<16>(int smem);
   template <>                                                                                          \
   cudaError_t detect_launch_kt<KTV>(const DetLaunch& L) {                                              \
     dim3 grid((L.P.N + DET_SC - 1) / DET_SC, L.P.T);                                                   \
-    dim3 block(32 * L.P.tiles.n_tiles);                                                                \
+    dim3 block(det_block_threads(L.P.tiles));                                                                \
     const bool d12 = L.P.D > 6;                                                                        \
     if (L.tma) {                                                                                       \
       if (d12) detect_kernel<KTV, 12, true><<<grid, block, L.smem, L.stream>>>(                        \

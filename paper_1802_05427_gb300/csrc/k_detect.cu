@@ -37,7 +37,8 @@ static int padded_users(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 :
 
 static size_t smem_bytes(const DetTiles& t, int K, int D, bool tma) {
   const int KT = padded_users(K), DT = D > 6 ? 12 : 6;
-  return 1024 + std::max(det_stage_bytes(t) * (tma ? DET_STAGES : 1), det_epilogue_bytes(KT, DT));
+  return 1024 + std::max(det_stage_bytes(t) * (tma ? DET_STAGES : 1),
+                         det_epilogue_bytes(KT, DT) + det_scratch_bytes(KT, DT));
 }
 
 static cudaError_t dispatch(DetLaunch& L) {

@@ -51,16 +51,16 @@ struct WSmall {
   float2 wt[BM * BM];  // tail block, zero padded
 };
 
+// acc = W v with the input index outermost, so the BM accumulators update independently.
 template <int BM>
 __device__ __forceinline__ void apply_w(const float2 (&W)[BM * BM], const float2 (&v)[BM],
                                         float2 (&acc)[BM]) {
 #pragma unroll
-  for (int i = 0; i < BM; ++i) {
-    float2 a = make_float2(0.f, 0.f);
+  for (int i = 0; i < BM; ++i) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < BM; ++j) cmac(a, W[i * BM + j], v[j]);
-    acc[i] = a;
-  }
+  for (int j = 0; j < BM; ++j)
+#pragma unroll
+    for (int i = 0; i < BM; ++i) cmac(acc[i], W[i * BM + j], v[j]);
 }
 
 template <int BM, bool LS>
@@ -178,9 +178,9 @@ __global__ void __launch_bounds__(STREAM_MAX_THREADS) lmmse_stream_kernel(
   for (int jp = 0; jp < BM / 2; ++jp) {
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active && 2 * jp < Bb) q = reinterpret_cast<const float4*>(pc + e0)[jp];
-    float inv = 1.0f / fmaf(q.x, q.x, q.y * q.y);
+    float inv = __fdividef(1.0f, fmaf(q.x, q.x, q.y * q.y));
     pcr[2 * jp] = (active && 2 * jp < Bb) ? make_float2(q.x * inv, -q.y * inv) : make_float2(0.f, 0.f);
-    inv = 1.0f / fmaf(q.z, q.z, q.w * q.w);
+    inv = __fdividef(1.0f, fmaf(q.z, q.z, q.w * q.w));
     pcr[2 * jp + 1] = (active && 2 * jp < Bb) ? make_float2(q.z * inv, -q.w * inv) : make_float2(0.f, 0.f);
   }
   for (int r = 0; r < nrows; ++r) {

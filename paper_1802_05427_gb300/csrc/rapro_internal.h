@@ -15,16 +15,24 @@ namespace rapro {
 constexpr int DET_SC = 16;
 constexpr int DET_MCH = 8;
 constexpr int DET_STAGES = 4;
-constexpr int DET_MAX_TILES = 16;   // K <= 16 and D <= 12 need at most 8 + 4*2 tiles
 
-// One thread tile of the detector's accumulation: 4 rows (users i) x 6 columns of the
-// augmented operand list [users 0..KP6-1 | data symbols 0..DP6-1].
+// Work roles of the detector's accumulation, one warp each (times an antenna split).
+// Users form groups of 4 (g = 0 .. NG-1), data symbols groups of 6.  A role is
+//   kind 0: the lower triangle of group g's Gram block plus, if r >= 0, the full
+//           Gram block of rows group r x columns group c (r > c);
+//   kind 1: only the block rows r x columns c;
+//   kind 2: matched-filter block of users group g x data symbols c*6 .. c*6+5.
+// Every needed entry of A (lower triangle) and z is computed exactly once.
+constexpr int DET_MAX_ROLES = 16;
 struct DetTiles {
-  int n_tiles;
-  int KP6;    // padded user rows in the shared-memory stage
-  int DP6;    // padded data rows
-  signed char row_group[DET_MAX_TILES];
-  signed char col_off[DET_MAX_TILES];
+  int n_roles;
+  int msplit;  // warps per role, each taking part of every antenna chunk
+  int KP;      // padded user rows in the shared-memory stage (4 * NG)
+  int DP;      // padded data rows (6 * data groups)
+  signed char kind[DET_MAX_ROLES];
+  signed char g[DET_MAX_ROLES];
+  signed char r[DET_MAX_ROLES];
+  signed char c[DET_MAX_ROLES];
 };
 
 constexpr int LMMSE_SMALL_MAX = 32;   // B <= this uses the weights-in-parameter kernel

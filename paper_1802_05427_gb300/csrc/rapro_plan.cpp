@@ -100,16 +100,32 @@ bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out
 
 DetTiles make_det_tiles(int K, int D) {
   DetTiles t{};
-  const int nrg = (K + 3) / 4, nug = (K + 5) / 6, ndg = (D + 5) / 6;
-  t.KP6 = std::max(4 * nrg, 6 * nug);
-  t.DP6 = 6 * ndg;
+  const int ng = (K + 3) / 4, ndg = (D + 5) / 6;
+  t.KP = 4 * ng;
+  t.DP = 6 * ndg;
   int n = 0;
-  for (int a = 0; a < nrg; ++a)
-    for (int c = 0; c < nug; ++c)
-      if (6 * c <= 4 * a + 3) { t.row_group[n] = (signed char)a; t.col_off[n] = (signed char)(6 * c); ++n; }
-  for (int a = 0; a < nrg; ++a)
-    for (int c = 0; c < ndg; ++c) { t.row_group[n] = (signed char)a; t.col_off[n] = (signed char)(t.KP6 + 6 * c); ++n; }
-  t.n_tiles = n;
+  auto add = [&](int kind, int g, int r, int c) {
+    t.kind[n] = (signed char)kind; t.g[n] = (signed char)g; t.r[n] = (signed char)r; t.c[n] = (signed char)c;
+    ++n;
+  };
+  // Off-diagonal Gram blocks (r > c): pair one with each triangle, the rest alone.
+  int rects[DET_MAX_ROLES][2], nr = 0;
+  for (int r = 1; r < ng; ++r)
+    for (int c = 0; c < r; ++c) { rects[nr][0] = r; rects[nr][1] = c; ++nr; }
+  bool used[DET_MAX_ROLES] = {};
+  for (int g = 0; g < ng; ++g) {
+    int pick = -1;
+    for (int k = 0; k < nr && pick < 0; ++k)   // prefer a block sharing rows or columns with g
+      if (!used[k] && (rects[k][0] == g || rects[k][1] == g)) pick = k;
+    if (pick >= 0) { used[pick] = true; add(0, g, rects[pick][0], rects[pick][1]); }
+    else add(0, g, -1, -1);
+  }
+  for (int k = 0; k < nr; ++k)
+    if (!used[k]) add(1, -1, rects[k][0], rects[k][1]);
+  for (int g = 0; g < ng; ++g)
+    for (int c = 0; c < ndg; ++c) add(2, g, -1, c);
+  t.n_roles = n;
+  t.msplit = n <= 8 ? 2 : 1;
   return t;
 }
 
