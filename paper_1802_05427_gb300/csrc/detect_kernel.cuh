@@ -12,11 +12,12 @@
 // between two warps per role.  A producer warp issues the TMA loads; consumer warps free a
 // stage through an mbarrier, so no CTA-wide barrier sits in the antenna loop.
 //
-// Epilogue, one half-warp per subcarrier:
-//   Cholesky of A + sigma2 I by columns, lane i holding row i (pivot and column broadcast
-//   by shuffles); L to shared memory; lane i computes column i of L^-1 by forward
-//   substitution (L reads broadcast) and s_i = sigma2 [A^-1]_ii = sigma2 sum_j |L^-1[j][i]|^2;
-//   w = L^-1 z lane-per-row and x~ = L^-H w lane-per-column, through shared memory.
+// Epilogue, one half-warp per subcarrier, lane i owning row i (all exchanges go through
+// shared memory: a broadcast load moves a complex value, a shuffle only half of one):
+//   Cholesky of A + sigma2 I by columns (each column published in a small buffer);
+//   column i of L^-1 by forward substitution with pending sums and
+//   s_i = sigma2 [A^-1]_ii = sigma2 sum_j |L^-1[j][i]|^2; w = L^-1 z lane-per-row and
+//   x~ = L^-H w lane-per-column.
 // Then all threads demap (x^ = x~ / mu, mu = 1 - s) and store with coalesced writes.
 #pragma once
 
@@ -49,12 +50,6 @@ struct DetLaunch {
   cudaStream_t stream;
 };
 
-// Shared-memory footprint of the epilogue for (KT, DT).
-__host__ __device__ constexpr size_t det_epilogue_bytes(int KT, int DT) {
-  return size_t(DET_SC) * KT * (KT + 1) * 8 + size_t(DET_SC) * KT * DT * 8 + size_t(DET_SC) * KT * 4 +
-         size_t(DET_SC) * 4;
-}
-
 // Threads of the largest role set of a (KT, DT) class (make_det_tiles at K = KT, D = DT):
 // NG triangle roles, the off-diagonal blocks left after pairing one with each triangle,
 // NG x data-group blocks; two warps per role when there are at most 8 roles.
@@ -70,9 +65,22 @@ inline int det_block_threads(const DetTiles& t) {
   return 32 * (warps < DET_SC / 2 ? DET_SC / 2 : warps);
 }
 
-// Partial sums of the second warp of each role, parked for the first (after A/z).
+// Shared-memory layout of the epilogue (reusing the stage ring), in float2 units:
+//   A / L / L^-1  [DET_SC][KT][KT+1]      z / w  [DET_SC][KT][DT]
+//   x~ [DT][KT][DET_SC+1]   s [KT][DET_SC+1] (float)   info [DET_SC] (int)
+//   column broadcast buffers [DET_SC][2][16]
+//   parked partial sums [warps][DET_SC][26]
+__host__ __device__ constexpr size_t det_off_z(int KT) { return size_t(DET_SC) * KT * (KT + 1); }
+__host__ __device__ constexpr size_t det_off_x(int KT, int DT) { return det_off_z(KT) + size_t(DET_SC) * KT * DT; }
+__host__ __device__ constexpr size_t det_off_s(int KT, int DT) { return det_off_x(KT, DT) + size_t(DT) * KT * (DET_SC + 1); }
+__host__ __device__ constexpr size_t det_off_col(int KT, int DT) {
+  return det_off_s(KT, DT) + (size_t(KT) * (DET_SC + 1) + DET_SC + 1) / 2;
+}
+__host__ __device__ constexpr size_t det_off_park(int KT, int DT) { return det_off_col(KT, DT) + size_t(DET_SC) * 2 * 16; }
+__host__ __device__ constexpr size_t det_epilogue_bytes(int KT, int DT) { return det_off_park(KT, DT) * 8; }
+// Parked partial sums: one slot of DET_SC x 26 complex per warp.
 __host__ __device__ constexpr size_t det_scratch_bytes(int KT, int DT) {
-  return size_t(det_max_threads(KT, DT) / 32) * 16 * 26 * 8;
+  return size_t(det_max_threads(KT, DT) / 32) * DET_SC * 26 * 8;
 }
 
 inline size_t det_stage_bytes(const DetTiles& t) {
@@ -300,35 +308,51 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     return;
   }
 
-  // Sum the antenna halves (lanes) and, with two warps per role, the two warps.
-#pragma unroll
-  for (int e = 0; e < 26; ++e) {
-    acc[e].x += __shfl_xor_sync(0xffffffffu, acc[e].x, 16);
-    acc[e].y += __shfl_xor_sync(0xffffffffu, acc[e].y, 16);
-  }
+  // ---------------- partial sums -> A (+ sigma2 I, lower triangle) and z
   constexpr int AS = KT + 1;                                    // padded row stride
-  float2* As = stage0;                                          // [DET_SC][KT][AS], later rows of L^-1
-  float2* Zs = As + DET_SC * KT * AS;                           // [DET_SC][KT][DT], later w, then x~ [n][k]
-  float* Ss = reinterpret_cast<float*>(Zs + DET_SC * KT * DT);  // [DET_SC][KT]  s_k
-  int* Is = reinterpret_cast<int*>(Ss + DET_SC * KT);           // [DET_SC]      info
-  float2* park = reinterpret_cast<float2*>(stage0) + det_epilogue_bytes(KT, DT) / sizeof(float2);
-  if (P.tiles.msplit == 2) {
-    if (mg == 1 && mh == 0) {
+  constexpr int XS = DET_SC + 1;
+  float2* As = stage0;                                          // [DET_SC][KT][AS]: A, then L, then L^-1
+  float2* Zs = stage0 + det_off_z(KT);                          // [DET_SC][KT][DT]: z, then w
+  float2* Xs = stage0 + det_off_x(KT, DT);                      // [DT][KT][XS]: x~
+  float* Ss = reinterpret_cast<float*>(stage0 + det_off_s(KT, DT));   // [KT][XS]: s_k
+  int* Is = reinterpret_cast<int*>(Ss + KT * XS);              // [DET_SC]: info
+  float2* Cb = stage0 + det_off_col(KT, DT);                    // [DET_SC][2][16]: column broadcast
+  float2* park = stage0 + det_off_park(KT, DT);                 // [warp][DET_SC][26]
+  if (consumer) {
+    float2* pw = park + size_t(warp) * DET_SC * 26 + sc * 26;
+    if (mh == 1) {
 #pragma unroll
-      for (int e = 0; e < 26; ++e) park[(role * 16 + sc) * 26 + e] = acc[e];
+      for (int e = 0; e < 26; ++e) pw[e] = acc[e];
     }
-    __syncthreads();
-    if (mg == 0 && mh == 0) {
+    __syncwarp();
+    if (mh == 0) {
 #pragma unroll
       for (int e = 0; e < 26; ++e) {
-        const float2 o = park[(role * 16 + sc) * 26 + e];
+        const float2 o = pw[e];
         acc[e].x += o.x;
         acc[e].y += o.y;
       }
     }
   }
-  // A (+ sigma2 I, lower triangle) and z to shared memory.
-  if (mg == 0 && mh == 0) {
+  if (P.tiles.msplit == 2) {
+    __syncthreads();                       // every warp has read its own slot
+    if (consumer && mg == 1 && mh == 0) {
+      float2* pw = park + size_t(role) * DET_SC * 26 + sc * 26;
+#pragma unroll
+      for (int e = 0; e < 26; ++e) pw[e] = acc[e];
+    }
+    __syncthreads();
+    if (consumer && mg == 0 && mh == 0) {
+      const float2* pw = park + size_t(role) * DET_SC * 26 + sc * 26;
+#pragma unroll
+      for (int e = 0; e < 26; ++e) {
+        const float2 o = pw[e];
+        acc[e].x += o.x;
+        acc[e].y += o.y;
+      }
+    }
+  }
+  if (consumer && mg == 0 && mh == 0) {
     if (kind == 2) {
 #pragma unroll
       for (int ii = 0; ii < 4; ++ii)
@@ -363,85 +387,87 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   __syncthreads();
 
   // --------------------------------------------- factorisation and solves
-  const int hw = lane >> 4, i = lane & 15, base = hw << 4;
-  const unsigned FULL = 0xffffffffu;
   // Every CTA has at least DET_SC / 2 warps, so each half-warp takes at most one subcarrier
-  // (a single pass keeps the row arrays in registers).
+  // (a single pass keeps the row arrays in registers).  Lane i owns row i.
+  const int hw = lane >> 4, i = lane & 15;
   const int scl = warp * 2 + hw;
   if (scl < DET_SC) {
     const bool live = i < K;                 // real user row
-    float2* Am = As + scl * KT * AS;         // this subcarrier: A, then L, then L^-1 (by columns)
-    float2* Zm = Zs + scl * KT * DT;         // z, then w, then x~ as [n][k]
+    const bool row = i < KT;                 // row of the padded system
+    float2* Am = As + scl * KT * AS;
+    float2* Zm = Zs + scl * KT * DT;
+    float2* cb = Cb + scl * 32;              // two 16-entry column buffers
     float2 ar[KT];
 #pragma unroll
     for (int j = 0; j < KT; ++j) {
       if (live && j <= i) ar[j] = Am[i * AS + j];
-      else ar[j] = make_float2((i < KT && j == i) ? 1.f : 0.f, 0.f);   // padded rows: identity
+      else ar[j] = make_float2((row && j == i) ? 1.f : 0.f, 0.f);   // padded rows: identity
     }
 
-    // Cholesky, column j at a time; every lane reads the pivot, so each knows 1 / L_jj.
+    // Cholesky, column j at a time: rows publish A[.][j] in a column buffer; every lane
+    // reads the pivot and the column from it (broadcast loads) and updates its own row.
     float inv_l[KT];
     int fail = 0;
 #pragma unroll
     for (int j = 0; j < KT; ++j) {
-      const float d = __shfl_sync(FULL, ar[j].x, base + j);
+      float2* col = cb + (j & 1) * 16;
+      if (row) col[i] = ar[j];
+      __syncwarp();
+      const float d = col[j].x;
       const bool ok = (d > 0.0f) && (d < 3.0e38f);
       if (!ok && fail == 0) fail = j + 1;
       const float il = rsqrtf(d);                            // 1 / L_jj
       inv_l[j] = il;
-      if (i == j) ar[j] = make_float2(d * il, 0.f);
-      else if (i > j) ar[j] = make_float2(ar[j].x * il, ar[j].y * il);
+      const float2 lij = make_float2(ar[j].x * il, ar[j].y * il);   // L[i][j] for i > j
 #pragma unroll
       for (int l = j + 1; l < KT; ++l) {
-        float2 c;
-        c.x = __shfl_sync(FULL, ar[j].x, base + l);          // L[l][j]
-        c.y = __shfl_sync(FULL, ar[j].y, base + l);
+        const float2 a = col[l];                             // A[l][j]; L[l][j] = a * il
         if (i >= l) {                                        // A[i][l] -= L[i][j] conj(L[l][j])
-          ar[l].x -= fmaf(ar[j].x, c.x, ar[j].y * c.y);
-          ar[l].y -= fmaf(ar[j].y, c.x, -ar[j].x * c.y);
+          ar[l].x -= fmaf(lij.x, a.x, lij.y * a.y) * il;
+          ar[l].y -= fmaf(lij.y, a.x, -lij.x * a.y) * il;
         }
       }
+      ar[j] = (i == j) ? make_float2(d * il, 0.f) : ((i > j) ? lij : ar[j]);
     }
-    __syncwarp();
-    if (i < KT) {
+    if (row) {
 #pragma unroll
-      for (int j = 0; j < KT; ++j) Am[i * AS + j] = ar[j];   // row i of L (zero above the diagonal)
+      for (int j = 0; j < KT; ++j) Am[i * AS + j] = ar[j];   // row i of L
     }
     __syncwarp();
-    // Column i of L^-1: y_i = 1 / L_ii, y_j = -(sum_{i <= l < j} L[j][l] y_l) / L_jj (j > i);
-    // the L[j][l] reads are the same address across lanes (broadcast).
-    float2 yc[KT];
+    // Column i of L^-1 by forward substitution with pending sums: once y_j is known, every
+    // later row r gets pend[r] += L[r][j] y_j (independent updates, broadcast loads).
+    float2 yc[KT], pend[KT];
+#pragma unroll
+    for (int r = 0; r < KT; ++r) pend[r] = make_float2(0.f, 0.f);
     float sk = 0.f;
 #pragma unroll
     for (int j = 0; j < KT; ++j) {
-      float2 acc2 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int l = 0; l < j; ++l) cmac(acc2, Am[j * AS + l], yc[l]);   // yc[l] = 0 for l < i
       const float il = inv_l[j];
-      yc[j] = (j == i) ? make_float2(il, 0.f) : ((j > i) ? make_float2(-acc2.x * il, -acc2.y * il)
-                                                           : make_float2(0.f, 0.f));
+      yc[j] = (j == i) ? make_float2(il, 0.f)
+                       : ((j > i) ? make_float2(-pend[j].x * il, -pend[j].y * il) : make_float2(0.f, 0.f));
       sk = fmaf(yc[j].x, yc[j].x, fmaf(yc[j].y, yc[j].y, sk));
+#pragma unroll
+      for (int r = j + 1; r < KT; ++r) cmac(pend[r], Am[r * AS + j], yc[j]);
     }
     __syncwarp();
-    if (i < KT) {
+    if (row) {
 #pragma unroll
       for (int j = 0; j < KT; ++j) Am[j * AS + i] = yc[j];   // L^-1[j][i]
     }
-    if (live) Ss[scl * KT + i] = P.sigma2 * sk;
+    if (live) Ss[i * XS + scl] = P.sigma2 * sk;
     if (i == 0) Is[scl] = fail;
     __syncwarp();
-    // w_i = sum_{l <= i} L^-1[i][l] z_l  (row i of L^-1; the z reads broadcast).
-    float2 wr[DT];
+    // w_i = sum_{l <= i} L^-1[i][l] z_l (row i of L^-1 first, then the broadcast z reads).
+    float2 yrow[KT], wr[DT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) yrow[l] = live ? Am[i * AS + l] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int n = 0; n < DT; ++n) wr[n] = make_float2(0.f, 0.f);
-    if (live) {
 #pragma unroll
-      for (int l = 0; l < KT; ++l) {
-        if (l < K) {
-          const float2 Y = Am[i * AS + l];
+    for (int l = 0; l < KT; ++l) {
+      if (l < K) {
 #pragma unroll
-          for (int n = 0; n < DT; ++n) cmac(wr[n], Y, Zm[l * DT + n]);
-        }
+        for (int n = 0; n < DT; ++n) cmac(wr[n], yrow[l], Zm[l * DT + n]);
       }
     }
     __syncwarp();
@@ -454,36 +480,33 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     float2 xr[DT];
 #pragma unroll
     for (int n = 0; n < DT; ++n) xr[n] = make_float2(0.f, 0.f);
-    if (live) {
 #pragma unroll
-      for (int j = 0; j < KT; ++j) {
-        if (j < K) {
+    for (int j = 0; j < KT; ++j) {
+      if (j < K) {
 #pragma unroll
-          for (int n = 0; n < DT; ++n) cmac_conj(xr[n], yc[j], Zm[j * DT + n]);
-        }
+        for (int n = 0; n < DT; ++n) cmac_conj(xr[n], yc[j], Zm[j * DT + n]);
       }
     }
-    __syncwarp();
     if (live) {
 #pragma unroll
       for (int n = 0; n < DT; ++n)
-        if (n < D) Zm[n * KT + i] = xr[n];                   // x~ as [n][k]
+        if (n < D) Xs[(n * KT + i) * XS + scl] = xr[n];
     }
-    __syncwarp();
   }
   __syncthreads();
 
   // ------------------------------------------------ demap and coalesced stores
   const int total = D * K * DET_SC;
+#pragma unroll 2
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int scx = idx % DET_SC, k = (idx / DET_SC) % K, n = idx / (DET_SC * K);
     const int kg = k0 + scx;
     if (kg >= N) continue;
-    const float2 xt = Zs[(scx * DT + n) * KT + k];
+    const float2 xt = Xs[(n * KT + k) * XS + scx];
     const size_t o = (size_t(t * D + n) * K + k) * N + kg;
     x_eq[o] = xt;
     if (labels || llr) {
-      const float s = Ss[scx * KT + k];
+      const float s = Ss[k * XS + scx];
       switch (P.q) {
         case 2: demap_store<1>(xt, s, o, labels, llr); break;
         case 4: demap_store<2>(xt, s, o, labels, llr); break;

@@ -135,9 +135,17 @@ __global__ void __launch_bounds__(SMALL_THREADS) lmmse_small_kernel(const float2
 constexpr int STREAM_ROWS = 8;
 constexpr int STREAM_BUF = 3;
 constexpr int STREAM_MAX_THREADS = 512;
+// Threads (= blocks per row) a streaming CTA may have for padded block size BM.
+__host__ __device__ constexpr int stream_max_threads(int BM) { return BM <= 12 ? STREAM_MAX_THREADS : 256; }
 
 template <int BM>
-__global__ void __launch_bounds__(STREAM_MAX_THREADS) lmmse_stream_kernel(
+__device__ __forceinline__ void apply_stream(const WSmall<BM>& W, bool tail, const float2 (&v)[BM], float2 (&acc)[BM]) {
+  if (!tail) apply_w<BM>(W.w, v, acc);
+  else apply_w<BM>(W.wt, v, acc);
+}
+
+template <int BM>
+__global__ void __launch_bounds__(stream_max_threads(BM)) lmmse_stream_kernel(
     const float2* __restrict__ y, const float2* __restrict__ pil, float2* __restrict__ out, int M, int N,
     int B, int nb, int tail, int* status, const __grid_constant__ WSmall<BM> W) {
   static_assert(BM % 2 == 0, "blocks move as pairs of complex values");
@@ -198,10 +206,7 @@ __global__ void __launch_bounds__(STREAM_MAX_THREADS) lmmse_stream_kernel(
         v[2 * jp] = make_float2(fmaf(q.x, c0.x, -q.y * c0.y), fmaf(q.x, c0.y, q.y * c0.x));
         v[2 * jp + 1] = make_float2(fmaf(q.z, c1.x, -q.w * c1.y), fmaf(q.z, c1.y, q.w * c1.x));
       }
-      if (!is_tail)
-        apply_w<BM>(W.w, v, acc);
-      else
-        apply_w<BM>(W.wt, v, acc);
+      apply_stream<BM>(W, is_tail, v, acc);
 #pragma unroll
       for (int jp = 0; jp < BM / 2; ++jp)
         if (2 * jp < Bb) row4[jp] = make_float4(acc[2 * jp].x, acc[2 * jp].y, acc[2 * jp + 1].x, acc[2 * jp + 1].y);
@@ -243,14 +248,16 @@ static void fill_small(WSmall<BM>& W, const float2* w_main, const float2* w_tail
 static bool stream_ok(const float2* y, const float2* pil, const float2* out, int N, int B, int nb) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(pil) |
                       reinterpret_cast<uintptr_t>(out);
-  return (a & 15) == 0 && N % 2 == 0 && B % 2 == 0 && nb <= STREAM_MAX_THREADS &&
+  const int bm = B <= 4 ? 4 : B <= 8 ? 8 : B <= 12 ? 12 : B <= 16 ? 16 : B <= 24 ? 24 : 32;
+  return (a & 15) == 0 && N % 2 == 0 && B % 2 == 0 && nb <= stream_max_threads(bm) &&
          lmmse_stream_smem(N) <= size_t(200) * 1024;
 }
 
 template <int BM>
-static cudaError_t launch_stream(const WSmall<BM>& W, const float2* y, const float2* pil, float2* out,
+static cudaError_t launch_stream(const WSmall<BM>& W0, const float2* y, const float2* pil, float2* out,
                                  int T, int K, int M, int N, int B, int nb, int tail, int* status,
                                  cudaStream_t st) {
+  const WSmall<BM>& W = W0;
   const size_t smem = lmmse_stream_smem(N);
   dim3 grid((M + STREAM_ROWS - 1) / STREAM_ROWS, T * K);
   const int threads = std::max(32, (nb + 31) / 32 * 32);
