@@ -34,6 +34,7 @@ METRIC = "uplink REs detected/s at 128x12, 1200 sc (FP32 vs BF16-TC); % roofline
 UNIT = "REs/s"
 N_SETS = 8                   # resident input subframes rotated through (> L2 in total)
 GRAPH_STEPS = N_SETS         # steps per captured CUDA graph
+IN_FLIGHT = 2                # subframes in flight: consecutive steps alternate between 2 streams
 L2_BYTES = 129 * 2 ** 20
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 
@@ -312,35 +313,47 @@ def run_rapro(args):
         sf = synth.make_subframe(sh, seed=synth.SEED_BASE + 1000 * rank + i)
         sets.append({k: torch.from_numpy(synth.as_c64(sf[k])).to(dev) for k in ("y_pilot", "pilots", "y_data")})
     in_bytes = sum(t.numel() * t.element_size() for t in sets[0].values())
-    h = torch.empty(s["h"], dtype=torch.complex64, device=dev)
-    x = torch.empty(s["x_eq"], dtype=torch.complex64, device=dev)
-    lab = torch.empty(s["labels"], dtype=torch.uint8, device=dev)
-    info = torch.empty(s["info"], dtype=torch.int32, device=dev)
+    # one output set per pipeline: consecutive subframes alternate between IN_FLIGHT streams
+    outs = [dict(h=torch.empty(s["h"], dtype=torch.complex64, device=dev),
+                 x=torch.empty(s["x_eq"], dtype=torch.complex64, device=dev),
+                 lab=torch.empty(s["labels"], dtype=torch.uint8, device=dev),
+                 info=torch.empty(s["info"], dtype=torch.int32, device=dev)) for _ in range(IN_FLIGHT)]
+    h, x, lab, info = outs[0]["h"], outs[0]["x"], outs[0]["lab"], outs[0]["info"]
 
-    def step(i, which=("est", "det")):
-        d = sets[i % N_SETS]
+    def step(i, which=("est", "det"), stream=None):
+        d, o = sets[i % N_SETS], outs[i % IN_FLIGHT]
         if "est" in which:
-            R.rapro_ce_ls_lmmse(plan, d["y_pilot"], d["pilots"], h)
+            R.rapro_ce_ls_lmmse(plan, d["y_pilot"], d["pilots"], o["h"], stream=stream)
         if "det" in which:
-            R.rapro_mmse_detect(plan, h, d["y_data"], x, lab, None, info)
+            R.rapro_mmse_detect(plan, o["h"], d["y_data"], o["x"], o["lab"], None, o["info"], stream=stream)
 
     # eager warm-up (also compiles nothing: kernels are prebuilt)
     for i in range(max(args.warmup, 3)):
         step(i)
     torch.cuda.synchronize()
 
-    def capture(which, n, start=0):
+    def capture(which, n, start=0, pipelines=1):
+        """Graph of steps start..start+n-1; step i runs on pipeline stream i % pipelines."""
         g = torch.cuda.CUDAGraph()
         st = torch.cuda.Stream()
+        side = [torch.cuda.Stream() for _ in range(pipelines)]
         st.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(st):
             with torch.cuda.graph(g, stream=st):
+                fork = torch.cuda.Event()
+                fork.record(st)
+                for q in side:
+                    q.wait_event(fork)
                 for i in range(start, start + n):
-                    step(i, which)
+                    step(i, which, stream=side[i % pipelines])
+                for q in side:
+                    join = torch.cuda.Event()
+                    join.record(q)
+                    st.wait_event(join)
         torch.cuda.synchronize()
         return g
 
-    g_full = capture(("est", "det"), GRAPH_STEPS)
+    g_full = capture(("est", "det"), GRAPH_STEPS, pipelines=IN_FLIGHT)
     g_one = [capture(("est", "det"), 1, j) for j in range(GRAPH_STEPS)]
     g_est = capture(("est",), GRAPH_STEPS)
     g_det = capture(("det",), GRAPH_STEPS)
@@ -486,7 +499,8 @@ def run_rapro(args):
                        "res_per_step": res_per_step, "parallelism": f"replicas x{world}",
                        "l2": f"{N_SETS} resident input subframes rotated ({N_SETS * in_bytes / 2**20:.0f} MiB > "
                              f"{L2_BYTES / 2**20:.0f} MiB L2)",
-                       "launch": f"CUDA graph replays of {GRAPH_STEPS} steps"},
+                       "launch": f"CUDA graph replays of {GRAPH_STEPS} steps; consecutive steps alternate "
+                                 f"between {IN_FLIGHT} streams, so {IN_FLIGHT} subframes are in flight"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * res_per_step * args.e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
