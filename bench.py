@@ -111,6 +111,22 @@ def measured_traffic(kernel):
     return None if v is None else float(v)
 
 
+# ------------------------------------------------------------ multi-rank
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest of every rank's value (a timed region ends when the slowest rank does)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, units_per_step: int, steps: int, ms: float) -> float:
+    """Units all ranks processed per second: every rank runs its own replica of the steps."""
+    return world * units_per_step * steps / (ms * 1e-3)
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -385,11 +401,7 @@ def run_rapro(args):
     t_host1 = time.time()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     time.sleep(0.25)
     clocks.stop()
     window = "1.5 s of sustained graph replays right before the timed region, plus the timed region"
@@ -430,11 +442,7 @@ def run_rapro(args):
         rx.receive_host(d["y_pilot"], d["pilots"], d["y_data"], x_h, lab_h)
     e1.record()
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     h2d = sum(t.numel() * t.element_size() for t in host_sets[0].values())
     d2h = x_h.numel() * x_h.element_size() + lab_h.numel()
 
@@ -471,7 +479,7 @@ def run_rapro(args):
         if dist:
             dist.destroy_process_group()
         return
-    value = world * res_per_step * args.steps / (ms * 1e-3)
+    value = whole_job_value(world, res_per_step, args.steps, ms)
     hbm, peak_kind = peaks()
     rows = {}
     for name, us in (("ls_lmmse", us_est), ("detect", us_det)):
@@ -502,7 +510,7 @@ def run_rapro(args):
                        "launch": f"CUDA graph replays of {GRAPH_STEPS} steps; consecutive steps alternate "
                                  f"between {IN_FLIGHT} streams, so {IN_FLIGHT} subframes are in flight"},
             "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": world * res_per_step * args.e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": whole_job_value(world, res_per_step, args.e2e_steps, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "Receiver.receive_host (pinned host in/out, rapro_receive_subframe)"},
             "gpu_launches": 2 * args.steps, "clocks": clk,

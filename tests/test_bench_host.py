@@ -1,0 +1,59 @@
+"""Host logic of bench.py's multi-rank path on CPU: two gloo ranks, no GPU.
+
+Replicas only: every rank times its own copy of the steps, the job's time is the slowest
+rank's, and the value counts the units of all ranks."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = bench.max_over_ranks(10.0 + 5.0 * rank, dist, torch.device("cpu"))
+    out[rank] = ms
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    world = 2
+    out = mp.Manager().dict()
+    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    assert out[0] == out[1] == 15.0
+
+
+def test_whole_job_value_counts_all_replicas():
+    assert bench.whole_job_value(1, 14400, 100, 2.0) == pytest.approx(14400 * 100 / 2e-3)
+    assert bench.whole_job_value(4, 14400, 100, 2.0) == pytest.approx(4 * 14400 * 100 / 2e-3)
+
+
+def test_single_process_needs_no_collective():
+    assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_algorithmic_bytes_and_flops_of_the_paper_scale_subframe():
+    """Per-launch figures the roofline divides by (one subframe, B = 12)."""
+    from paper_1802_05427_gb300 import synth
+    a = bench.algorithmic(synth.PAPER_SCALE, 12)
+    n_h = 2 * 12 * 128 * 1200
+    assert a["res_per_step"] == 14400
+    assert a["ls_lmmse"]["bytes"] == 8 * n_h + 8 * 2 * 12 * 1200 + 8 * n_h + 8 * 144
+    assert a["ls_lmmse"]["flops"] == 6 * n_h + 8 * 12 * n_h
+    det = a["detect"]
+    assert det["bytes"] == 8 * n_h + 8 * 12 * 128 * 1200 + 8 * 12 * 12 * 1200 + 12 * 12 * 1200 + 4 * 2 * 1200
+    assert det["flops"] == 2400 * (8 * 128 * 78 + 8 * 12 ** 3 // 6) + 14400 * (8 * 128 * 12 + 8 * 144)
