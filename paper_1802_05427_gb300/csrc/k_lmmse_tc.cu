@@ -1,0 +1,416 @@
+// LS + sub-block LMMSE (Eq. 9, 12, 17) on the 5th-generation tensor cores (tcgen05).
+//
+// With B dividing n_sc, every (slot, user, antenna) row splits into nb blocks and all full
+// blocks share W.  The LS estimates then form one matrix X with R * nb rows ("row-blocks")
+// of B complex values, stored contiguously in y_pilot's layout, and the filter is the GEMM
+//   H = X W^T  (complex)  =  X_r Wr^T  in the interleaved real embedding,
+// X_r: rows x 2B floats (re, im, re, im, ...), Wr[2i][2j] = Re W[i][j], Wr[2i][2j+1] =
+// -Im W[i][j], Wr[2i+1][2j] = Im W[i][j], Wr[2i+1][2j+1] = Re W[i][j].
+//
+// FP32 accuracy on TF32 tensor cores: every operand is split x = hi + lo (both TF32) and
+// D = Ah Wh^T + Ah Wl^T + Al Wh^T, accumulated in FP32 in tensor memory.
+//
+// Persistent CTAs work through contiguous runs of tiles of 128 row-blocks (B * 1 KB,
+// contiguous in memory), with three roles:
+//  * a copy warp: 1-D bulk copies of raw tiles into a ring of stages, and one bulk store
+//    per filtered tile, after which the stage takes the next load;
+//  * 256 consumer threads, two per row-block (one per half of its reals): the LS estimate
+//    y conj(p) / |p|^2, split into TF32 hi and lo in the canonical K-major layout (8-row x
+//    16-byte core matrices) of one of two A buffers; then, for the previous tile, the
+//    accumulator row read back from tensor memory (tcgen05.ld, TMEM lane = row-block) and
+//    written over the raw stage;
+//  * an MMA warp: one thread issues the MMAs of a tile (M = 128, N = 32, K = 8 each) into
+//    one of two accumulators as soon as its A buffer is complete, and commits them to an
+//    mbarrier.
+// Only mbarriers order the roles, so the LS of tile i+1 runs while the tensor cores work
+// on tile i and the copies of other tiles are in flight.
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
+#include "rapro_internal.h"
+#include "rapro_ptx.cuh"
+
+namespace rapro {
+
+namespace {
+
+constexpr int TC_ROWS = 128;        // row-blocks per tile (MMA M, TMEM lanes)
+constexpr int TC_N = 32;            // MMA N: 2B <= 32 output reals, padded with zero weights
+constexpr int TC_STAGES = 4;        // raw-tile ring depth
+constexpr int TC_CONSUMERS = 256;    // two threads per row-block, one per half of its reals
+constexpr int TC_THREADS = TC_CONSUMERS + 64;   // + one MMA warp + one copy warp
+
+// High part of the split x = hi + lo: x truncated to TF32 (10 explicit mantissa bits), so
+// that lo = x - hi is exact in FP32; the MMA reads lo at TF32 precision, an error of at
+// most 2^-20 |x|.
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 bytes,
+// lbo = byte distance between cores adjacent along K, sbo = between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((smem_u32(p) >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = TC_N.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TC_N >> 3) << 17) |
+                                (uint32_t(TC_ROWS >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescTf32), "r"(accumulate ? 1 : 0)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+}  // namespace
+
+template <int KR>
+__global__ void __launch_bounds__(TC_THREADS) lmmse_tc_kernel(const float2* __restrict__ y,
+                                                              const float2* __restrict__ pil,
+                                                              float2* __restrict__ out, int M, int N, int B,
+                                                              long long n_rb, int n_tiles, int* status,
+                                                              const float* __restrict__ w_tc) {
+  static_assert(KR % 8 == 0 && KR <= 32, "2B padded to a multiple of 8, at most 32");
+  constexpr uint32_t SBO = (KR / 4) * 128;                      // 8-row group stride (A and B)
+  constexpr int A_BYTES = TC_ROWS * KR * 4;
+  constexpr int B_BYTES = TC_N * KR * 4;
+  constexpr int KQ = KR / 4;                                    // float4 (2 complex) per row-block
+  constexpr int KH = KQ / 2;                                    // float4 per consumer thread
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);           // [TC_STAGES] raw tile landed
+  uint64_t* epi = full + TC_STAGES;                             // [TC_STAGES] tile written back
+  uint64_t* aready = epi + TC_STAGES;                           // [2] A buffer holds a tile
+  uint64_t* done = aready + 2;                                  // [2] MMAs of an A buffer finished
+  uint64_t* wbar = done + 2;                                    // weights landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  unsigned char* sA = smem + 1024;                              // [2 buffers][hi, lo][A_BYTES]
+  unsigned char* sBh = sA + 4 * A_BYTES;
+  unsigned char* sBl = sBh + B_BYTES;
+  float2* raw = reinterpret_cast<float2*>(sBl + B_BYTES);       // [TC_STAGES][TC_ROWS * B]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile_elems = TC_ROWS * B;
+  const int nb = N / B;
+  (void)sBl;
+
+  if (tid == 0) {
+    for (int st = 0; st < TC_STAGES; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&epi[st], TC_CONSUMERS);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&aready[b], TC_CONSUMERS);
+      mbar_init(&done[b], 1);
+    }
+    mbar_init(wbar, 1);
+    *s_abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {   // two accumulators of TC_N columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * TC_N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // Each CTA takes a contiguous run of tiles: its row-blocks then share few pilot rows,
+  // which stay in L1 after the first tile.
+  const int t_begin = int((long long)n_tiles * blockIdx.x / gridDim.x);
+  const int my_tiles = int((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) - t_begin;
+  auto tile_of = [&](int it) { return t_begin + it; };
+  auto tile_count = [&](int it) -> int {
+    const long long left = n_rb - (long long)tile_of(it) * TC_ROWS;
+    return int(left < TC_ROWS ? left : TC_ROWS);
+  };
+  auto give_up = [&]() {
+    *s_abort = 1;
+    atomicExch(status, int(RAPRO_ERR_TIMEOUT));
+  };
+
+  if (warp == TC_CONSUMERS / 32 + 1) {
+    // ------------------------------------------------ copy warp: loads and stores
+    if (lane == 0 && my_tiles > 0) {
+      auto issue = [&](int it) {
+        const int st = it % TC_STAGES;
+        const uint32_t bytes = uint32_t(tile_count(it)) * B * sizeof(float2);
+        mbar_arrive_expect_tx(&full[st], bytes);
+        bulk_load(raw + size_t(st) * tile_elems, y + (size_t)tile_of(it) * tile_elems, bytes, &full[st]);
+      };
+      // The weights arrive already in the canonical layout (hi, then lo, 2 * B_BYTES).
+      mbar_arrive_expect_tx(wbar, 2 * B_BYTES);
+      bulk_load(sBh, w_tc, 2 * B_BYTES, wbar);
+      int issued = 0;
+      for (; issued < TC_STAGES && issued < my_tiles; ++issued) issue(issued);
+      bool bad = false;
+      for (int it = 0; it < my_tiles; ++it) {
+        const int st = it % TC_STAGES;
+        if (!mbar_wait_bounded(&epi[st], uint32_t(it / TC_STAGES) & 1u) || *s_abort) {
+          bad = true;
+          break;
+        }
+        bulk_store(out + (size_t)tile_of(it) * tile_elems, raw + size_t(st) * tile_elems,
+                   uint32_t(tile_count(it)) * B * sizeof(float2));
+        bulk_commit();
+        if (it + TC_STAGES < my_tiles) {
+          bulk_wait_read<0>();                 // the store has read the stage
+          issue(issued);
+          ++issued;
+        }
+      }
+      bulk_wait_all();
+      // Let every load land before the CTA exits (on the normal path all have been consumed):
+      // load j of stage s is phase j of full[s], the last one (issued - 1 - s) / TC_STAGES.
+      for (int s2 = 0; s2 < TC_STAGES && s2 < issued; ++s2)
+        (void)mbar_wait_bounded(&full[s2], uint32_t((issued - 1 - s2) / TC_STAGES) & 1u);
+      (void)mbar_wait_bounded(wbar, 0u);
+      if (bad) give_up();
+    }
+  } else if (warp == TC_CONSUMERS / 32) {
+    // ------------------------------------------------ MMA warp: one thread issues
+    if (lane == 0 && my_tiles > 0) {
+      bool bad = !mbar_wait_bounded(wbar, 0u);
+      int issued = 0;
+      for (int it = 0; it < my_tiles && !bad; ++it) {
+        const int buf = it & 1;
+        if (!mbar_wait_bounded(&aready[buf], uint32_t(it >> 1) & 1u) || *s_abort) {
+          bad = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // D[buf] = Ah Wh^T + Ah Wl^T + Al Wh^T over K = KR in steps of 8.
+        const unsigned char* ah = sA + buf * 2 * A_BYTES;
+        const unsigned char* al = ah + A_BYTES;
+        const uint32_t d = tmem + uint32_t(buf * TC_N);
+#pragma unroll
+        for (int kg = 0; kg < KR / 8; ++kg) {
+          const uint64_t dah = smem_desc(ah + kg * 256, 128, SBO), dal = smem_desc(al + kg * 256, 128, SBO);
+          const uint64_t dbh = smem_desc(sBh + kg * 256, 128, SBO), dbl = smem_desc(sBh + B_BYTES + kg * 256, 128, SBO);
+          mma_tf32(d, dah, dbh, kg > 0);
+          mma_tf32(d, dah, dbl, true);
+          mma_tf32(d, dal, dbh, true);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done[buf]))
+                     : "memory");
+        ++issued;
+      }
+      if (bad) {
+        // The tensor cores finish in order: wait for the last group before TMEM is freed.
+        if (issued > 0) (void)mbar_wait_bounded(&done[(issued - 1) & 1], uint32_t((issued - 1) >> 1) & 1u);
+        give_up();
+      }
+    }
+  } else {
+    // ------------------------------------------------ consumers: LS + split, read-back
+    const int r = tid & (TC_ROWS - 1), half = tid / TC_ROWS;   // row-block of the tile, half of it
+    // Pilots of this thread's row-block of tile it (B complex, two per float4).
+    auto load_pilots = [&](int it, float4 (&pv)[KH]) {
+      if (it >= my_tiles || r >= tile_count(it)) return;
+      const uint32_t rb = uint32_t(tile_of(it)) * TC_ROWS + uint32_t(r);   // n_rb < 2^31
+      const uint32_t row = rb / uint32_t(nb), b = rb - row * uint32_t(nb);
+      const float4* pr = reinterpret_cast<const float4*>(pil + size_t(row / uint32_t(M)) * N + size_t(b) * B);
+#pragma unroll
+      for (int j = 0; j < KH; ++j) {
+        const int kg = half * KH + j;
+        if (2 * kg < B) pv[j] = __ldg(pr + kg);
+      }
+    };
+    // LS estimate (y conj(p) / |p|^2) split into TF32 hi and lo, canonical K-major layout.
+    auto ls_split = [&](int it, const float4 (&pv)[KH], int buf) {
+      unsigned char* ah = sA + buf * 2 * A_BYTES;
+      unsigned char* al = ah + A_BYTES;
+      const bool live = r < tile_count(it);
+      const float4* x4 = reinterpret_cast<const float4*>(raw + size_t(it % TC_STAGES) * tile_elems + r * B);
+#pragma unroll
+      for (int j = 0; j < KH; ++j) {
+        const int kg = half * KH + j;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live && 2 * kg < B) {
+          const float4 x = x4[kg], p = pv[j];
+          const float i0 = __fdividef(1.0f, fmaf(p.x, p.x, p.y * p.y));
+          const float i1 = __fdividef(1.0f, fmaf(p.z, p.z, p.w * p.w));
+          q = make_float4(fmaf(x.x, p.x, x.y * p.y) * i0, fmaf(x.y, p.x, -x.x * p.y) * i0,
+                          fmaf(x.z, p.z, x.w * p.w) * i1, fmaf(x.w, p.z, -x.z * p.w) * i1);
+        }
+        const float4 h = make_float4(tf32_hi(q.x), tf32_hi(q.y), tf32_hi(q.z), tf32_hi(q.w));
+        const float4 l = make_float4(q.x - h.x, q.y - h.y, q.z - h.z, q.w - h.w);
+        const int off = (r / 8) * SBO + kg * 128 + (r % 8) * 16;
+        *reinterpret_cast<float4*>(ah + off) = h;
+        *reinterpret_cast<float4*>(al + off) = l;
+      }
+    };
+    // Accumulator row r (this warp's quarter of the TMEM lanes) over the raw tile; the
+    // branch on half is warp-uniform and keeps every register index static.
+    auto epilogue = [&](int it) -> bool {
+      const int buf = it & 1;
+      if (!mbar_wait_bounded(&done[buf], uint32_t(it >> 1) & 1u)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[32];
+      tmem_ld32(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(buf * TC_N), v);
+      float4* o4 = reinterpret_cast<float4*>(raw + size_t(it % TC_STAGES) * tile_elems + r * B);
+      const bool live = r < tile_count(it);
+      auto put = [&](auto hc) {
+        constexpr int H = decltype(hc)::value;
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+          const int kg = H * KH + j;
+          if (live && 2 * kg < B)
+            o4[kg] = make_float4(__uint_as_float(v[4 * kg]), __uint_as_float(v[4 * kg + 1]),
+                                 __uint_as_float(v[4 * kg + 2]), __uint_as_float(v[4 * kg + 3]));
+        }
+      };
+      if (half == 0) put(std::integral_constant<int, 0>{});
+      else put(std::integral_constant<int, 1>{});
+      fence_proxy_async_shared();              // the bulk store reads what was written here
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&epi[it % TC_STAGES]);
+      return true;
+    };
+    float4 pv[KH];
+#pragma unroll
+    for (int j = 0; j < KH; ++j) pv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    load_pilots(0, pv);
+    bool bad = false;
+    // Tile it's LS runs while the tensor cores work on tile it - 1.
+    for (int it = 0; it < my_tiles; ++it) {
+      if (*s_abort || !mbar_wait_bounded(&full[it % TC_STAGES], uint32_t(it / TC_STAGES) & 1u)) {
+        bad = true;
+        break;
+      }
+      ls_split(it, pv, it & 1);               // A buffer it & 1 was last read by MMA it - 2
+      load_pilots(it + 1, pv);
+      fence_proxy_async_shared();              // the MMAs read what was written here
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&aready[it & 1]);
+      if (it >= 1 && !epilogue(it - 1)) {
+        bad = true;
+        break;
+      }
+    }
+    if (!bad && my_tiles > 0 && !epilogue(my_tiles - 1)) bad = true;
+    if (bad) give_up();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N) : "memory");
+}
+
+template <int KR>
+static size_t tc_smem_bytes(int B) {
+  return 1024 + 4 * size_t(TC_ROWS) * KR * 4 + 2 * size_t(TC_N) * KR * 4 +
+         size_t(TC_STAGES) * TC_ROWS * B * sizeof(float2);
+}
+
+static float tf32_host(float x) {
+  // Round to nearest (ties away) at 10 explicit mantissa bits, as cvt.rna.tf32.f32.
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u = (u + 0x1000u) & 0xffffe000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+static int kr_for(int B) { return (2 * B + 7) / 8 * 8; }
+
+template <int KR>
+static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
+  const int B = pl.B, M = pl.p.M, N = pl.p.n_sc, R = pl.T * pl.p.K * pl.p.M;
+  const long long n_rb = (long long)R * (N / B);
+  const int n_tiles = int((n_rb + TC_ROWS - 1) / TC_ROWS);
+  int dev = 0, sms = 148, smem_sm = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const size_t smem = tc_smem_bytes<KR>(B);
+  // Resident CTAs per SM: shared memory, threads (2048 per SM) and tensor memory (512 columns).
+  int per_sm = int(size_t(smem_sm) / (smem + size_t(reserved)));
+  per_sm = std::max(1, std::min({per_sm, 2048 / TC_THREADS, 512 / (2 * TC_N)}));
+  const int grid = std::min(n_tiles, per_sm * sms);
+  lmmse_tc_kernel<KR><<<grid, TC_THREADS, smem, st>>>(y, pil, out, M, N, B, n_rb, n_tiles, pl.d_status, pl.d_w_tc);
+  return cudaGetLastError();
+}
+
+bool lmmse_tc_shape_ok(const Plan& pl) {
+  const long long n_rb = (long long)pl.T * pl.p.K * pl.p.M * (pl.p.n_sc / pl.B);
+  return pl.B % 2 == 0 && pl.B <= 16 && pl.tail == 0 && n_rb < (1ll << 31);
+}
+
+// The filter as the MMA's B operand: Wr (TC_N x KR reals, zero padded) in the canonical
+// K-major layout, its TF32 hi part followed by its lo part.
+void build_lmmse_tc_weights(const Plan& pl, std::vector<float>& out) {
+  const int B = pl.B, KR = kr_for(B);
+  const int SBO = (KR / 4) * 128, per = TC_N * KR;
+  out.assign(2 * size_t(per), 0.f);
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) {
+      const float2 v = pl.w_main[size_t(i) * B + j];
+      const float vals[2][2] = {{v.x, -v.y}, {v.y, v.x}};   // [out re/im][in re/im]
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) {
+          const int n = 2 * i + a, k = 2 * j + c;
+          const size_t off = size_t((n / 8) * SBO + (k / 4) * 128 + (n % 8) * 16 + (k % 4) * 4) / 4;
+          const float f = vals[a][c], h = tf32_host(f);
+          out[off] = h;
+          out[per + off] = tf32_host(f - h);
+        }
+    }
+}
+
+bool lmmse_tc_ok(const Plan& pl, const float2* y, const float2* pil, const float2* out) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(pil) |
+                      reinterpret_cast<uintptr_t>(out);
+  return pil != nullptr && pl.d_w_tc != nullptr && (a & 15) == 0 && lmmse_tc_shape_ok(pl);
+}
+
+cudaError_t launch_lmmse_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
+  switch (kr_for(pl.B)) {
+    case 8: return launch_tc<8>(pl, y, pil, out, st);
+    case 16: return launch_tc<16>(pl, y, pil, out, st);
+    case 24: return launch_tc<24>(pl, y, pil, out, st);
+    default: return launch_tc<32>(pl, y, pil, out, st);
+  }
+}
+
+cudaError_t prepare_lmmse_tc(int device) {
+  static std::once_flag flags[64];
+  static cudaError_t result[64];
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  std::call_once(flags[device], [device] {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(lmmse_tc_kernel<8>, A, int(tc_smem_bytes<8>(4)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<16>, A, int(tc_smem_bytes<16>(8)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<24>, A, int(tc_smem_bytes<24>(12)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<32>, A, int(tc_smem_bytes<32>(16)));
+    result[device] = e;
+  });
+  return result[device];
+}
+
+}  // namespace rapro

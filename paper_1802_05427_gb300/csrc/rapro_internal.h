@@ -47,6 +47,7 @@ struct Plan {
   float2* d_w_tail = nullptr;
   float2* d_h_work = nullptr;      // [T][K][M][n_sc] estimate workspace
   int* d_status = nullptr;         // device status word
+  float* d_w_tc = nullptr;         // tensor-core filter operand (canonical layout, hi then lo), or null
   DetTiles tiles{};
   int device = 0;
 };
@@ -74,6 +75,12 @@ cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
 
 cudaError_t prepare_detect(int device);
 cudaError_t prepare_estimate(int device);
+cudaError_t prepare_lmmse_tc(int device);
+// Tensor-core LS + LMMSE (even B <= 16 dividing n_sc, aligned arrays).
+bool lmmse_tc_shape_ok(const Plan& pl);
+void build_lmmse_tc_weights(const Plan& pl, std::vector<float>& out);
+bool lmmse_tc_ok(const Plan& pl, const float2* y, const float2* pil, const float2* out);
+cudaError_t launch_lmmse_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st);
 
 cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
                           unsigned char* labels, float* llr, int* info, cudaStream_t st);

@@ -245,9 +245,11 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDevice"); }
   if ((e = prepare_detect(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "detector set-up"); }
   if ((e = prepare_estimate(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "estimator set-up"); }
+  if ((e = prepare_lmmse_tc(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core estimator set-up"); }
   const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
+    cudaFree(pl->d_w_tc);
     delete pl;
     return cuda_fail(err, what);
   };
@@ -261,6 +263,13 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if (pl->tail && (e = cudaMemcpy(pl->d_w_tail, pl->w_tail.data(), pl->w_tail.size() * sizeof(float2),
                                   cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W tail");
   if ((e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset status");
+  if (lmmse_tc_shape_ok(*pl)) {
+    std::vector<float> wtc;
+    build_lmmse_tc_weights(*pl, wtc);
+    if ((e = cudaMalloc(&pl->d_w_tc, wtc.size() * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc W (tensor cores)");
+    if ((e = cudaMemcpy(pl->d_w_tc, wtc.data(), wtc.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(e, "cudaMemcpy W (tensor cores)");
+  }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan upload");
   *out = reinterpret_cast<rapro_plan*>(pl);
   return RAPRO_OK;
@@ -274,6 +283,7 @@ rapro_status rapro_plan_destroy(rapro_plan* plan) {
   cudaFree(pl->d_w_tail);
   cudaFree(pl->d_h_work);
   cudaFree(pl->d_status);
+  cudaFree(pl->d_w_tc);
   delete pl;
   return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, "rapro_plan_destroy");
 }

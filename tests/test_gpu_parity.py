@@ -162,6 +162,34 @@ def test_lmmse_weight_override(B):
     assert rel_err_per(_host(h), ref, axes=(2, 3)).max() <= TOL
 
 
+LS_LMMSE_CASES = [
+    # M, K, N, n_fft, B: even B <= 16 dividing N runs on the tensor cores (tiles ragged in the
+    # antennas and in the blocks, several tiles per CTA); the rest on the FP32 cores
+    (8, 2, 72, 128, 12), (5, 3, 100, 256, 10), (6, 2, 96, 128, 16), (3, 2, 90, 128, 6),
+    (2, 1, 64, 128, 2), (4, 3, 120, 256, 8), (7, 2, 84, 128, 14), (128, 12, 1200, 2048, 4),
+    (128, 12, 1200, 2048, 12), (128, 12, 1200, 2048, 16), (5, 3, 100, 256, 12), (5, 3, 100, 256, 7),
+    (128, 12, 1200, 2048, 48), (130, 1, 48, 128, 12), (200, 2, 32, 128, 16),
+]
+
+
+@pytest.mark.parametrize("case", LS_LMMSE_CASES)
+def test_ls_lmmse_parity(case):
+    """LS (Eq. 9) and the sub-block filter (Eq. 12, 17) in one call, against both oracle steps."""
+    M, K, N, nfft, B = case
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=24 if nfft >= 2048 else 6,
+                             tau_rms=8.0 if nfft >= 2048 else 4.0, snr_db=10.0, qam_bits=2)
+    sf, c64 = _inputs(sh, 4)
+    plan = R.Plan(params_for(sh, B))
+    h = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
+    R.rapro_ce_ls_lmmse(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), h)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    h_ls = O.ls_estimate(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128))
+    ref = O.subblock_lmmse(h_ls, B, oracle_r(sh), sh.sigma2)
+    e = rel_err_per(_host(h), ref, axes=(2, 3))
+    assert e.max() <= TOL, e.max()
+
+
 # ----------------------------------------------------------------- detection
 DETECT_CASES = [
     # M, K, N, D, q
