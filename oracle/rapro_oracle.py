@@ -28,6 +28,11 @@ Readings of points the paper leaves open (each also listed in the design notes):
     r(d) = sum_l p_l exp(-j 2 pi l d / n_fft), p_l ~ exp(-l / tau_rms), sum p_l = 1;
   * sub-blocks are contiguous and non-overlapping from subcarrier 0; the last one has
     N_sc mod B subcarriers and its own W;
+  * comb pilots (3W / 12W, Sec. IV-B): user k on tones k + iS; groups and windows as in
+    Tables I and II (the last 12W group is subcarriers 1189..1200 in the paper's 1-based
+    numbering: the printed 1190:1:1200 has 11 entries); 3W estimates and the three-fold
+    interpolated LS are zero-order held to every subcarrier (Sec. IV-C); past the last
+    tone the interpolated LS holds that tone's LS;
   * Gray QAM per dimension, unit mean energy; hard decision = nearest point;
     max-log LLR_i = (min_{b_i=1} |x^ - x|^2 - min_{b_i=0} |x^ - x|^2) / nu with the
     unbiased x^ = x~ / mu, mu_k = 1 - sigma2 [A^-1]_kk, nu = (1 - mu) / mu.
@@ -228,6 +233,131 @@ def boundary_margin(xhat: np.ndarray, q: int) -> np.ndarray:
     for comp in (np.real(xhat) * scale, np.imag(xhat) * scale):
         dist.append(np.min(np.abs(comp[..., None] - bounds), axis=-1))
     return np.minimum(dist[0], dist[1])
+
+
+# ------------------------------------------------- comb pilots (Sec. II, IV-B)
+# The paper's deployed pilot structure: the pilot OFDM symbol is shared by the users on
+# disjoint tones, user k (0-based) on subcarriers k, k + S, k + 2S, ... (Sec. II, Fig. 1;
+# S = 12 there).  Layouts: y_pilot [T][M][N_sc], pilots [T][N_sc] (the value sent on each
+# tone by its owner), h_ls [T][K][M][P] on the P = N_sc / S tones of each user.
+COMB_3W, COMB_SW, COMB_INTERP3 = "3W", "SW", "interp3"
+
+
+def comb_tones(k: int, S: int, n_sc: int) -> np.ndarray:
+    """Pilot subcarriers of user k: k, k + S, ... < n_sc (Sec. II)."""
+    return np.arange(k, n_sc, S)
+
+
+def comb_ls(y_pilot: np.ndarray, pilots: np.ndarray, K: int, S: int) -> np.ndarray:
+    """Eq. 9 on each user's own tones: h_ls[t][k][m][i] = y_p[t][m][k + iS] / p[t][k + iS]."""
+    y_pilot = np.asarray(y_pilot, dtype=np.complex128)
+    pilots = np.asarray(pilots, dtype=np.complex128)
+    n_sc = y_pilot.shape[-1]
+    out = []
+    for k in range(K):
+        tn = comb_tones(k, S, n_sc)
+        out.append(y_pilot[:, :, tn] / pilots[:, None, tn])
+    return np.stack(out, axis=1)
+
+
+def comb_groups(method: str, k: int, S: int, n_sc: int) -> list:
+    """Group map of Table I (3W) and Table II (S-W, 12W at S = 12) for user k, 0-based.
+
+    One group per pilot index j = 0..P-1, each a list of estimated subcarriers, the first
+    of the Q consecutive LS tones it uses (window i0) and the index of its weight matrix:
+      3W:  Q = 3, estimates at the user's tone j and S/3, 2S/3 after it;
+      S-W: Q = S, estimates at the S subcarriers jS .. jS + S - 1 (the same for all users);
+      window i0 = min(max(j - (Q - 1) // 2, 0), P - Q), weight index j - i0 (edge groups
+      get their own W, all interior groups share one, Sec. IV-B).
+    """
+    P = len(comb_tones(k, S, n_sc))
+    Q = 3 if method == COMB_3W else S
+    half = (Q - 1) // 2
+    groups = []
+    for j in range(P):
+        i0 = min(max(j - half, 0), P - Q)
+        if method == COMB_3W:
+            out = k + j * S + np.arange(3) * (S // 3)
+        else:
+            out = j * S + np.arange(S)
+        groups.append((out, i0, j - i0))
+    return groups
+
+
+def comb_weight(out_sc, in_sc, r, sigma2: float) -> np.ndarray:
+    """Eq. 17 with a rectangular cross-correlation (Eq. W1-W3, P):
+    W = R_{H Hls} (R_{Hls Hls} + sigma2 I)^-1, R_{H Hls}[a][b] = r(out_a - in_b),
+    R_{Hls Hls}[a][b] = r(in_a - in_b)."""
+    return lmmse_weight(corr_matrix(out_sc, in_sc, r), corr_matrix(in_sc, in_sc, r), sigma2)
+
+
+def zero_order_hold(pos: np.ndarray, vals: np.ndarray, n_sc: int) -> np.ndarray:
+    """Every subcarrier n takes the estimate at the last position <= n (Sec. IV-C, on the
+    detector's input); subcarriers before the first position take the first estimate."""
+    order = np.argsort(pos, kind="stable")
+    pos, vals = np.asarray(pos)[order], vals[..., order]
+    idx = np.searchsorted(pos, np.arange(n_sc), side="right") - 1
+    return vals[..., np.maximum(idx, 0)]
+
+
+def comb_lmmse(h_ls: np.ndarray, method: str, S: int, n_sc: int, r, sigma2: float) -> np.ndarray:
+    """3W- / S-W-LMMSE (Sec. IV-B): per group, W (Q estimates x Q LS tones) times the
+    group's LS window (Eq. 12); 3W estimates are then held to every subcarrier.
+    Returns h [T][K][M][n_sc]."""
+    h_ls = np.asarray(h_ls, dtype=np.complex128)
+    T, K, M, _ = h_ls.shape
+    out = np.empty((T, K, M, n_sc), dtype=np.complex128)
+    for k in range(K):
+        tones = comb_tones(k, S, n_sc)
+        pos, vals = [], []
+        for o, i0, _ in comb_groups(method, k, S, n_sc):
+            Q = 3 if method == COMB_3W else S
+            W = comb_weight(o, tones[i0:i0 + Q], r, sigma2)
+            pos.append(o)
+            vals.append(h_ls[:, k, :, i0:i0 + Q] @ W.T)
+        pos = np.concatenate(pos)
+        vals = np.concatenate(vals, axis=-1)
+        if method == COMB_3W:
+            out[:, k] = zero_order_hold(pos, vals, n_sc)
+        else:
+            keep = pos < n_sc
+            out[:, k][..., pos[keep]] = vals[..., keep]
+    return out
+
+
+def comb_interp3_ls(h_ls: np.ndarray, S: int, n_sc: int) -> np.ndarray:
+    """Three-fold linearly interpolated LS (Sec. III-A, the comparator of Sec. V): at the
+    3W positions k + jS + uS/3 the LS of tones j and j+1 weighted (1 - u/3, u/3); past the
+    last tone its LS is held; then zero-order hold to every subcarrier."""
+    h_ls = np.asarray(h_ls, dtype=np.complex128)
+    T, K, M, P = h_ls.shape
+    out = np.empty((T, K, M, n_sc), dtype=np.complex128)
+    for k in range(K):
+        pos, vals = [], []
+        for j in range(P):
+            for u in range(3):
+                pos.append(k + j * S + u * (S // 3))
+                if j + 1 < P:
+                    vals.append((1 - u / 3) * h_ls[:, k, :, j] + (u / 3) * h_ls[:, k, :, j + 1])
+                else:
+                    vals.append(h_ls[:, k, :, j])
+        out[:, k] = zero_order_hold(np.array(pos), np.stack(vals, axis=-1), n_sc)
+    return out
+
+
+def comb_receive_subframe(y_pilot, pilots, y_data, *, K: int, S: int, method: str, sigma2: float, r,
+                          n_data_per_slot: int, q: int) -> dict:
+    """Comb-pilot LS -> 3W / S-W LMMSE or interpolated LS -> MMSE detection -> demap."""
+    n_sc = np.asarray(y_pilot).shape[-1]
+    h_ls = comb_ls(y_pilot, pilots, K, S)
+    if method == COMB_INTERP3:
+        h = comb_interp3_ls(h_ls, S, n_sc)
+    else:
+        h = comb_lmmse(h_ls, method, S, n_sc, r, sigma2)
+    x_eq, s = mmse_detect(h, y_data, sigma2, n_data_per_slot)
+    xhat, nu = unbias(x_eq, s, n_data_per_slot)
+    return dict(h_ls=h_ls, h=h, x_eq=x_eq, s=s, xhat=xhat, nu=nu,
+                labels=hard_decision(xhat, q), llr=maxlog_llr(xhat, nu, q))
 
 
 # ---------------------------------------------------------------- whole path

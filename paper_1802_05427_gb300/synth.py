@@ -8,7 +8,8 @@ correlation model, no LMMSE weights, no detection, no demapping).  What it does:
   normalised to unit total power (Sec. III-A model under Eq. 16, Table III uses
   integer delays too), taken to the frequency domain over ``n_fft`` bins (Eq. 1-5);
 * unit-modulus pilots with seeded phases, one pilot observation per user and slot
-  (idealised orthogonal pilots: y_p = H p + n, Eq. 5 with one active user);
+  (idealised orthogonal pilots: y_p = H p + n, Eq. 5 with one active user), or the comb
+  of Sec. II (user k on tones k, k + S, ...; ``make_comb_subframe``);
 * uniform payload labels mapped to Gray QAM (transmitter side): per dimension
   m = q/2 bits, read MSB first, even-indexed label bits on I and odd-indexed on Q,
   level = (2^m - 1) - 2 * gray_to_binary(bits), scaled to unit mean energy;
@@ -122,6 +123,48 @@ def make_subframe(shape: SubframeShape, seed: int, noiseless: bool = False,
     x = gray_qam_map(labels, sh.qam_bits)
     n_d = _cn(rng, (sh.n_data, sh.M, sh.n_sc), sigma2)
     y_data = np.einsum("mkn,dkn->dmn", H, x) + n_d
+    return dict(H=H, pilots=pilots, y_pilot=y_pilot, labels=labels, x=x,
+                y_data=y_data, sigma2=sigma2, taps=taps, pdp=p_l)
+
+
+def make_comb_subframe(shape: SubframeShape, seed: int, S: int, noiseless: bool = False,
+                       tap_powers: Optional[np.ndarray] = None) -> dict:
+    """Draw one subframe with the comb pilot structure of Sec. II (Fig. 1).
+
+    The pilot OFDM symbol of each slot is shared: user k owns the tones n with n mod S == k
+    (tones of offsets >= K carry no user, only noise).  ``tap_powers`` (optional) replaces
+    the exponential profile with given tap powers at delays 0, 1, ... (normalised).
+
+    Returns, besides H, labels, x, y_data and sigma2 as in make_subframe:
+      pilots   [n_slots][n_sc]       unit-modulus value sent on each tone by its owner
+      y_pilot  [n_slots][M][n_sc]    received pilot symbol
+    """
+    sh = shape
+    if sh.K > S:
+        raise ValueError("K users need at least K comb offsets")
+    rng = np.random.default_rng(seed)
+    if tap_powers is None:
+        p_l = pdp_exponential(sh.n_taps, sh.tau_rms)
+    else:
+        p_l = np.asarray(tap_powers, dtype=np.float64)
+        p_l = p_l / p_l.sum()
+    n_taps = p_l.size
+    taps = _cn(rng, (sh.M, sh.K, n_taps), p_l[None, None, :])
+    k = np.arange(sh.n_sc, dtype=np.float64)
+    l = np.arange(n_taps, dtype=np.float64)
+    H = taps @ np.exp(-2j * np.pi * np.outer(l, k) / sh.n_fft)    # [M][K][n_sc]
+
+    pilots = np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=(sh.n_slots, sh.n_sc)))
+    owner = np.arange(sh.n_sc) % S
+    sigma2 = 0.0 if noiseless else sh.sigma2
+    Hown = np.zeros((sh.M, sh.n_sc), dtype=np.complex128)
+    live = owner < sh.K
+    Hown[:, live] = H[:, owner[live], np.arange(sh.n_sc)[live]]
+    y_pilot = Hown[None] * pilots[:, None, :] + _cn(rng, (sh.n_slots, sh.M, sh.n_sc), sigma2)
+
+    labels = rng.integers(0, 1 << sh.qam_bits, size=(sh.n_data, sh.K, sh.n_sc))
+    x = gray_qam_map(labels, sh.qam_bits)
+    y_data = np.einsum("mkn,dkn->dmn", H, x) + _cn(rng, (sh.n_data, sh.M, sh.n_sc), sigma2)
     return dict(H=H, pilots=pilots, y_pilot=y_pilot, labels=labels, x=x,
                 y_data=y_data, sigma2=sigma2, taps=taps, pdp=p_l)
 
