@@ -38,6 +38,11 @@
  *   llr               [T*D][K][n_sc][q] max-log LLR per bit, b0 first, > 0 favours 0
  *   info              [T][n_sc]         0, or j+1 if pivot j of the Cholesky factor of
  *                                       H^H H + sigma2 I was not positive and finite
+ * With pilot_layout == RAPRO_PILOT_COMB (the shared pilot symbol of Sec. II, user s on
+ * the tones s, s + S, s + 2S, ... of a comb of spacing S = comb_spacing):
+ *   y_pilot           [T][M][n_sc]      received pilot OFDM symbol of each slot
+ *   pilots            [T][n_sc]         value sent on each tone by the user owning it
+ *   h                 [T][K][M][n_sc]   dense channel estimate, as above
  */
 #ifndef RAPRO_H
 #define RAPRO_H
@@ -66,8 +71,23 @@ typedef enum {
 
 typedef enum {
   RAPRO_PILOT_ORTHOGONAL = 0,  /* one pilot observation per user on every subcarrier */
-  RAPRO_PILOT_COMB = 1         /* the FDM comb of Sec. II: not implemented (UNSUPPORTED) */
+  RAPRO_PILOT_COMB = 1         /* the FDM comb of Sec. II, estimated by rapro_ce_comb */
 } rapro_pilot_layout;
+
+/* Estimators of the comb layout (Sec. IV-B; groups and windows of Tables I and II). */
+typedef enum {
+  /* 3W-LMMSE: per pilot tone j of a user, 3 estimates at the tone and S/3, 2S/3 after it
+   * from the LS of 3 consecutive tones (window min(max(j-1, 0), P-3)), one of 3 weight
+   * matrices shared by all users; zero-order hold to every subcarrier.  3 | S. */
+  RAPRO_COMB_3W = 0,
+  /* S-W-LMMSE (12W at S = 12): per group j, the S subcarriers jS .. jS+S-1 from the LS of
+   * S consecutive tones (window min(max(j-(S-1)/2, 0), P-S)), one of S weight matrices
+   * per user. */
+  RAPRO_COMB_SW = 1,
+  /* Three-fold linearly interpolated LS at the 3W positions (the comparator of Sec. V),
+   * the last tone's LS held past it, then zero-order hold.  3 | S. */
+  RAPRO_COMB_INTERP3 = 2
+} rapro_comb_method;
 
 typedef enum {
   /* Exponential power-delay profile of Sec. III-A (text under Eq. 16) on integer delays:
@@ -99,6 +119,10 @@ typedef struct {
   double tau_rms;        /* EXP: decay constant in samples, > 0 */
   double L;              /* UNIFORM_L: assumed channel length in samples, > 0 */
   int qam_bits;          /* q = 2 (QPSK), 4 (16-QAM) or 6 (64-QAM) */
+  /* pilot_layout == RAPRO_PILOT_COMB only (ignored otherwise; subblock is then unused): */
+  int comb_spacing;      /* S: tone spacing of each user's comb, K <= S <= 16, S | n_sc,
+                            P = n_sc / S tones per user, 2 <= P <= 1024, P >= the window */
+  int comb_method;       /* rapro_comb_method */
 } rapro_params;
 
 typedef struct rapro_plan rapro_plan;
@@ -122,9 +146,21 @@ rapro_status rapro_params_validate(const rapro_params* p);
 rapro_status rapro_build_weights_host(const rapro_params* p, int block_len, double* w_out);
 
 /*
+ * Host-only FP64 weights of the comb estimators (pilot_layout == RAPRO_PILOT_COMB,
+ * comb_method 3W or S-W; Sec. IV-B, Eq. 17 with Eq. W1-W3 and P).  Q = 3 (3W) or S (S-W);
+ * sets = 1 (3W, shared by all users) or K (S-W, one per user).  w_out receives
+ * sets * Q * Q * Q complex doubles, interleaved {re, im}: set k, weight index w (the
+ * group's position in its window, Tables I-II: W^(w+1)), row u (estimate), column i
+ * (window tone) at 2 * (((k*Q + w)*Q + u)*Q + i).
+ * Returns RAPRO_ERR_NOT_POSDEF if R_{Hls Hls} + sigma2 I fails to factor in FP64.
+ */
+rapro_status rapro_build_comb_weights_host(const rapro_params* p, double* w_out);
+
+/*
  * Validate p, build W_b for the full block size B and for the tail block of
- * n_sc mod B subcarriers (blocks start at subcarrier 0), round them to
- * complex64, copy them to the current device, and allocate the workspace.
+ * n_sc mod B subcarriers (blocks start at subcarrier 0), or the comb weights of
+ * rapro_build_comb_weights_host for a comb plan, round them to complex64, copy them to
+ * the current device, and allocate the workspace.
  * Synchronous.  *out is NULL on failure.
  */
 rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out);
@@ -189,9 +225,22 @@ rapro_status rapro_mmse_detect(const rapro_plan* plan, const rapro_c32* h,
                                float* llr, int32_t* info, rapro_stream stream);
 
 /*
- * The whole path (a1, a3, a4-a8) for one subframe: rapro_ce_ls_lmmse, then
- * rapro_mmse_detect, on the same stream.  h_out (nullable) receives the LMMSE channel
- * estimate; when NULL the plan's workspace holds it.  Other arguments as above.
+ * Comb-pilot channel estimation (plans with pilot_layout == RAPRO_PILOT_COMB; Sec. II,
+ * IV-B): the LS estimate of Eq. 9 on each user's tones, then the plan's comb_method
+ * (3W- or S-W-LMMSE: W = R_{H Hls} (R_{Hls Hls} + sigma2 I)^-1 of Eq. 17 with the
+ * rectangular cross-correlation of Eq. W1-W3 and P, per group of Tables I and II; or
+ * three-fold interpolated LS), and zero-order hold, into the dense h [T][K][M][n_sc] the
+ * detector reads.  The weights are built in FP64 at plan creation.  Layouts in the header
+ * comment.  Orthogonal-layout plans return RAPRO_ERR_UNSUPPORTED (and comb plans do so
+ * for rapro_ce_ls, rapro_ce_lmmse_subblock and rapro_ce_ls_lmmse).
+ */
+rapro_status rapro_ce_comb(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
+                           rapro_c32* h, rapro_stream stream);
+
+/*
+ * The whole path (a1, a3, a4-a8) for one subframe: rapro_ce_ls_lmmse (rapro_ce_comb for a
+ * comb plan), then rapro_mmse_detect, on the same stream.  h_out (nullable) receives the
+ * channel estimate; when NULL the plan's workspace holds it.  Other arguments as above.
  */
 rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_pilot,
                                     const rapro_c32* pilots, const rapro_c32* y_data,
@@ -206,7 +255,8 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
  * allocator, and processes whose device memory belongs to another framework's pool.
  *  - Needs no plan: p is validated and the weights of its sub-block size are built in
  *    FP64 on the host at every call and passed to the kernel as parameters, so subblock
- *    must be <= 32 (RAPRO_ERR_UNSUPPORTED otherwise).
+ *    must be <= 32 (RAPRO_ERR_UNSUPPORTED otherwise); the comb layout is not available
+ *    here (RAPRO_ERR_UNSUPPORTED).
  *  - The channel-estimate scratch is a fixed 32 MiB device array inside the library
  *    (held by every GPU that loads the library until the process exits):
  *    n_pilot_sym * K * M * n_sc * 8 bytes must not exceed 32 MiB (RAPRO_ERR_INVALID_ARG

@@ -27,6 +27,12 @@ rapro_status launched(cudaError_t e, const char* what) {
   return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, what);
 }
 
+rapro_status orthogonal_only(const Plan* pl) {
+  if (!pl->comb) return RAPRO_OK;
+  set_error("this estimator reads the orthogonal pilot layout; comb plans use rapro_ce_comb");
+  return RAPRO_ERR_UNSUPPORTED;
+}
+
 inline const float2* f2(const rapro_c32* p) { return reinterpret_cast<const float2*>(p); }
 inline float2* f2(rapro_c32* p) { return reinterpret_cast<float2*>(p); }
 inline cudaStream_t cs(rapro_stream s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -41,6 +47,7 @@ rapro_status rapro_ce_ls(const rapro_plan* plan, const rapro_c32* y_pilot, const
   if (!y_pilot || !pilots || !h_ls) return bad("y_pilot, pilots and h_ls must not be NULL");
   const Plan* pl = reinterpret_cast<const Plan*>(plan);
   rapro_status s = check_device(pl);
+  if (s == RAPRO_OK) s = orthogonal_only(pl);
   if (s != RAPRO_OK) return s;
   return launched(launch_ls(f2(y_pilot), f2(pilots), f2(h_ls), pl->T, pl->p.K, pl->p.M, pl->p.n_sc, cs(stream)),
                   "LS kernel launch");
@@ -53,6 +60,7 @@ rapro_status rapro_ce_lmmse_subblock(const rapro_plan* plan, const rapro_c32* h_
   if (f2(h_ls) == f2(h)) return bad("h must not alias h_ls");
   const Plan* pl = reinterpret_cast<const Plan*>(plan);
   rapro_status s = check_device(pl);
+  if (s == RAPRO_OK) s = orthogonal_only(pl);
   if (s != RAPRO_OK) return s;
   const float2* w = w_override ? f2(w_override) : pl->d_w_main;
   return launched(launch_lmmse(*pl, f2(h_ls), nullptr, w, pl->d_w_tail, pl->w_main.data(),
@@ -67,11 +75,26 @@ rapro_status rapro_ce_ls_lmmse(const rapro_plan* plan, const rapro_c32* y_pilot,
   if (f2(y_pilot) == f2(h)) return bad("h must not alias y_pilot");
   const Plan* pl = reinterpret_cast<const Plan*>(plan);
   rapro_status s = check_device(pl);
+  if (s == RAPRO_OK) s = orthogonal_only(pl);
   if (s != RAPRO_OK) return s;
   const float2* w = w_override ? f2(w_override) : pl->d_w_main;
   return launched(launch_lmmse(*pl, f2(y_pilot), f2(pilots), w, pl->d_w_tail, pl->w_main.data(),
                                pl->w_tail.data(), f2(h), cs(stream)),
                   "LS+LMMSE kernel launch");
+}
+
+rapro_status rapro_ce_comb(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
+                           rapro_c32* h, rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  if (!y_pilot || !pilots || !h) return bad("y_pilot, pilots and h must not be NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  rapro_status s = check_device(pl);
+  if (s != RAPRO_OK) return s;
+  if (!pl->comb) {
+    set_error("rapro_ce_comb needs a plan with pilot_layout == RAPRO_PILOT_COMB");
+    return RAPRO_ERR_UNSUPPORTED;
+  }
+  return launched(launch_comb(*pl, f2(y_pilot), f2(pilots), f2(h), cs(stream)), "comb estimator launch");
 }
 
 rapro_status rapro_mmse_detect(const rapro_plan* plan, const rapro_c32* h, const rapro_c32* y_data,
@@ -97,9 +120,10 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
   rapro_status s = check_device(pl);
   if (s != RAPRO_OK) return s;
   float2* h = h_out ? f2(h_out) : pl->d_h_work;
-  cudaError_t e = launch_lmmse(*pl, f2(y_pilot), f2(pilots), pl->d_w_main, pl->d_w_tail,
-                               pl->w_main.data(), pl->w_tail.data(), h, cs(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "LS+LMMSE kernel launch");
+  cudaError_t e = pl->comb ? launch_comb(*pl, f2(y_pilot), f2(pilots), h, cs(stream))
+                           : launch_lmmse(*pl, f2(y_pilot), f2(pilots), pl->d_w_main, pl->d_w_tail,
+                                          pl->w_main.data(), pl->w_tail.data(), h, cs(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "channel estimator launch");
   return launched(launch_detect(*pl, h, f2(y_data), f2(x_eq), labels, llr, info, cs(stream)),
                   "detection kernel launch");
 }

@@ -48,6 +48,9 @@ struct Plan {
   float2* d_h_work = nullptr;      // [T][K][M][n_sc] estimate workspace
   int* d_status = nullptr;         // device status word
   float* d_w_tc = nullptr;         // tensor-core filter operand (canonical layout, hi then lo), or null
+  bool comb = false;               // comb pilot layout (Sec. II)
+  std::vector<float2> w_comb;      // comb weights [sets][Q][Q][Q] (3W: 1 set, S-W: K sets)
+  float2* d_w_comb = nullptr;
   DetTiles tiles{};
   int device = 0;
 };
@@ -61,6 +64,12 @@ rapro_status cuda_fail(cudaError_t e, const char* what);
 bool build_weights_fp64(const rapro_params& p, int len, std::vector<double>& w);
 
 DetTiles make_det_tiles(int K, int D);
+
+// Comb layout: window Q (3 or S) and the FP64 weights [sets][w][u][i], interleaved.
+int comb_window(const rapro_params& p);
+bool build_comb_weights_fp64(const rapro_params& p, std::vector<double>& w_out);
+cudaError_t launch_comb(const Plan& pl, const float2* y, const float2* pil, float2* h, cudaStream_t st);
+cudaError_t prepare_comb(int device);
 
 // Kernel launchers (return the launch error, if any).
 cudaError_t launch_ls(const float2* y, const float2* pil, float2* h, int T, int K, int M,

@@ -132,6 +132,8 @@ extern "C" rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, co
   if (s != RAPRO_OK) return s;
   if (!y_pilot || !pilots || !y_data || !x_eq)
     return reject(RAPRO_ERR_INVALID_ARG, "y_pilot, pilots, y_data and x_eq must not be NULL");
+  if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL)
+    return reject(RAPRO_ERR_UNSUPPORTED, "the allocation-free receive reads the orthogonal pilot layout only");
   if (p->subblock > LMMSE_SMALL_MAX)
     return reject(RAPRO_ERR_UNSUPPORTED, "the allocation-free receive needs subblock <= 32");
   const int T = p->n_pilot_sym, D = p->n_sym / p->n_pilot_sym - 1;

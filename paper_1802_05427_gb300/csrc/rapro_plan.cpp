@@ -98,6 +98,64 @@ bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out
   return true;
 }
 
+int comb_window(const rapro_params& p) {
+  return p.comb_method == RAPRO_COMB_SW ? p.comb_spacing : 3;
+}
+
+bool build_comb_weights_fp64(const rapro_params& p, std::vector<double>& w_out) {
+  // Sec. IV-B: per weight index w (group position within its window) a Q x Q matrix
+  // W = R_o (R_i + sigma2 I)^-1, R_i[a][b] = r((a - b) S) over the window's tones and
+  // R_o[u][i] = r(out_u - tone_i):  (w - i) S + u S/3 for 3W (any user), (w - i) S + u - k
+  // for S-W and user k.  Solved as for the sub-blocks: A = L L^H, X = A^-1 R_o^H, W = X^H.
+  const int S = p.comb_spacing, Q = comb_window(p);
+  const bool sw = p.comb_method == RAPRO_COMB_SW;
+  const int sets = sw ? p.K : 1;
+  std::vector<cd> L(size_t(Q) * Q), X(size_t(Q) * Q), y(Q);
+  for (int i = 0; i < Q; ++i)
+    for (int j = 0; j <= i; ++j) L[size_t(i) * Q + j] = corr(p, (i - j) * S) + (i == j ? p.sigma2 : 0.0);
+  for (int j = 0; j < Q; ++j) {
+    cd* Lj = &L[size_t(j) * Q];
+    double d = Lj[j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(Lj[k]);
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    const double ljj = std::sqrt(d);
+    Lj[j] = cd(ljj, 0.0);
+    for (int i = j + 1; i < Q; ++i) {
+      cd* Li = &L[size_t(i) * Q];
+      cd s = Li[j];
+      for (int k = 0; k < j; ++k) s -= Li[k] * std::conj(Lj[k]);
+      Li[j] = s / ljj;
+    }
+  }
+  w_out.assign(size_t(2) * sets * Q * Q * Q, 0.0);
+  for (int k = 0; k < sets; ++k)
+    for (int w = 0; w < Q; ++w) {
+      auto off = [&](int u, int i) { return sw ? (w - i) * S + u - k : (w - i) * S + u * (S / 3); };
+      // column c of R_o^H: conj(R_o[c][i]) over i; solve L y = col, L^H x = y.
+      for (int c = 0; c < Q; ++c) {
+        for (int i = 0; i < Q; ++i) {
+          cd s = std::conj(corr(p, off(c, i)));
+          const cd* Li = &L[size_t(i) * Q];
+          for (int m = 0; m < i; ++m) s -= Li[m] * y[m];
+          y[i] = s / Li[i].real();
+        }
+        for (int i = Q - 1; i >= 0; --i) {
+          cd s = y[i];
+          for (int m = i + 1; m < Q; ++m) s -= std::conj(L[size_t(m) * Q + i]) * X[size_t(m) * Q + c];
+          X[size_t(i) * Q + c] = s / L[size_t(i) * Q + i].real();
+        }
+      }
+      double* dst = &w_out[size_t(2) * ((size_t(k) * Q + w) * Q) * Q];
+      for (int u = 0; u < Q; ++u)
+        for (int i = 0; i < Q; ++i) {
+          const cd v = std::conj(X[size_t(i) * Q + u]);   // W[u][i] = conj(X[i][u])
+          dst[2 * (size_t(u) * Q + i)] = v.real();
+          dst[2 * (size_t(u) * Q + i) + 1] = v.imag();
+        }
+    }
+  return true;
+}
+
 DetTiles make_det_tiles(int K, int D) {
   DetTiles t{};
   const int ng = (K + 3) / 4, ndg = (D + 5) / 6;
@@ -172,11 +230,24 @@ rapro_status rapro_params_validate(const rapro_params* p) {
     if (p->pilot_sym_idx[j] < j * slot_len || p->pilot_sym_idx[j] >= (j + 1) * slot_len)
       return invalid("pilot_sym_idx[j] must lie inside slot j");
   if (p->pilot_layout == RAPRO_PILOT_COMB) {
-    set_error("comb pilot layout is not implemented");
-    return RAPRO_ERR_UNSUPPORTED;
+    const int S = p->comb_spacing;
+    if (S < p->K || S > 16) return invalid("comb_spacing must be in [K, 16]");
+    if (p->n_sc % S != 0) return invalid("comb_spacing must divide n_sc");
+    const int P = p->n_sc / S;
+    if (P > 1024) return invalid("more than 1024 pilot tones per user");
+    if (p->comb_method == RAPRO_COMB_SW) {
+      if (P < S) return invalid("S-W-LMMSE needs at least comb_spacing tones per user");
+    } else if (p->comb_method == RAPRO_COMB_3W || p->comb_method == RAPRO_COMB_INTERP3) {
+      if (S % 3 != 0) return invalid("3W-LMMSE and interpolated LS need 3 | comb_spacing");
+      if (P < 3) return invalid("3W-LMMSE and interpolated LS need at least 3 tones per user");
+    } else {
+      return invalid("unknown comb_method");
+    }
+  } else if (p->pilot_layout == RAPRO_PILOT_ORTHOGONAL) {
+    if (p->subblock < 1 || p->subblock > p->n_sc) return invalid("subblock must be in [1, n_sc]");
+  } else {
+    return invalid("unknown pilot_layout");
   }
-  if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL) return invalid("unknown pilot_layout");
-  if (p->subblock < 1 || p->subblock > p->n_sc) return invalid("subblock must be in [1, n_sc]");
   if (!(p->sigma2 > 0.0) || !std::isfinite(p->sigma2)) return invalid("sigma2 must be finite and > 0");
   if (p->pdp == RAPRO_PDP_EXP) {
     if (p->n_taps < 1) return invalid("n_taps must be >= 1");
@@ -206,6 +277,21 @@ rapro_status rapro_build_weights_host(const rapro_params* p, int block_len, doub
   return RAPRO_OK;
 }
 
+rapro_status rapro_build_comb_weights_host(const rapro_params* p, double* w_out) {
+  rapro_status s = rapro_params_validate(p);
+  if (s != RAPRO_OK) return s;
+  if (p->pilot_layout != RAPRO_PILOT_COMB || p->comb_method == RAPRO_COMB_INTERP3)
+    return invalid("weights exist for the comb layout's 3W and S-W methods only");
+  if (!w_out) return invalid("w_out is NULL");
+  std::vector<double> w;
+  if (!build_comb_weights_fp64(*p, w)) {
+    set_error("R_{Hls Hls} + sigma2 I is not positive definite in FP64");
+    return RAPRO_ERR_NOT_POSDEF;
+  }
+  std::memcpy(w_out, w.data(), w.size() * sizeof(double));
+  return RAPRO_OK;
+}
+
 rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if (!out) return invalid("out is NULL");
   *out = nullptr;
@@ -216,9 +302,12 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   pl->T = p->n_pilot_sym;
   pl->D = p->n_sym / p->n_pilot_sym - 1;
   pl->q = p->qam_bits;
-  pl->B = p->subblock;
-  pl->nb = (p->n_sc + p->subblock - 1) / p->subblock;
-  pl->tail = p->n_sc % p->subblock;
+  pl->comb = p->pilot_layout == RAPRO_PILOT_COMB;
+  if (!pl->comb) {
+    pl->B = p->subblock;
+    pl->nb = (p->n_sc + p->subblock - 1) / p->subblock;
+    pl->tail = p->n_sc % p->subblock;
+  }
   pl->tiles = make_det_tiles(p->K, pl->D);
 
   auto to_c64 = [](const std::vector<double>& w) {
@@ -227,12 +316,22 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
     return o;
   };
   std::vector<double> w;
-  if (!build_weights_fp64(*p, pl->B, w)) {
+  if (pl->comb) {
+    if (p->comb_method != RAPRO_COMB_INTERP3) {
+      if (!build_comb_weights_fp64(*p, w)) {
+        delete pl;
+        set_error("R_{Hls Hls} + sigma2 I is not positive definite in FP64");
+        return RAPRO_ERR_NOT_POSDEF;
+      }
+      pl->w_comb = to_c64(w);
+    }
+  } else if (!build_weights_fp64(*p, pl->B, w)) {
     delete pl;
     set_error("R_b + sigma2 I is not positive definite in FP64");
     return RAPRO_ERR_NOT_POSDEF;
+  } else {
+    pl->w_main = to_c64(w);
   }
-  pl->w_main = to_c64(w);
   if (pl->tail) {
     if (!build_weights_fp64(*p, pl->tail, w)) {
       delete pl;
@@ -246,24 +345,32 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if ((e = prepare_detect(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "detector set-up"); }
   if ((e = prepare_estimate(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "estimator set-up"); }
   if ((e = prepare_lmmse_tc(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core estimator set-up"); }
+  if ((e = prepare_comb(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "comb estimator set-up"); }
   const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
-    cudaFree(pl->d_w_tc);
+    cudaFree(pl->d_w_tc); cudaFree(pl->d_w_comb);
     delete pl;
     return cuda_fail(err, what);
   };
-  if ((e = cudaMalloc(&pl->d_w_main, pl->w_main.size() * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc W");
+  if (!pl->w_main.empty() &&
+      (e = cudaMalloc(&pl->d_w_main, pl->w_main.size() * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc W");
+  if (!pl->w_comb.empty()) {
+    if ((e = cudaMalloc(&pl->d_w_comb, pl->w_comb.size() * sizeof(float2))) != cudaSuccess)
+      return fail(e, "cudaMalloc W (comb)");
+    if ((e = cudaMemcpy(pl->d_w_comb, pl->w_comb.data(), pl->w_comb.size() * sizeof(float2),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W (comb)");
+  }
   if (pl->tail && (e = cudaMalloc(&pl->d_w_tail, pl->w_tail.size() * sizeof(float2))) != cudaSuccess)
     return fail(e, "cudaMalloc W tail");
   if ((e = cudaMalloc(&pl->d_h_work, h_elems * sizeof(float2))) != cudaSuccess) return fail(e, "cudaMalloc workspace");
   if ((e = cudaMalloc(&pl->d_status, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc status");
-  if ((e = cudaMemcpy(pl->d_w_main, pl->w_main.data(), pl->w_main.size() * sizeof(float2),
-                      cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W");
+  if (!pl->w_main.empty() && (e = cudaMemcpy(pl->d_w_main, pl->w_main.data(), pl->w_main.size() * sizeof(float2),
+                                             cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W");
   if (pl->tail && (e = cudaMemcpy(pl->d_w_tail, pl->w_tail.data(), pl->w_tail.size() * sizeof(float2),
                                   cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W tail");
   if ((e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset status");
-  if (lmmse_tc_shape_ok(*pl)) {
+  if (!pl->comb && lmmse_tc_shape_ok(*pl)) {
     std::vector<float> wtc;
     build_lmmse_tc_weights(*pl, wtc);
     if ((e = cudaMalloc(&pl->d_w_tc, wtc.size() * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc W (tensor cores)");
@@ -284,6 +391,7 @@ rapro_status rapro_plan_destroy(rapro_plan* plan) {
   cudaFree(pl->d_h_work);
   cudaFree(pl->d_status);
   cudaFree(pl->d_w_tc);
+  cudaFree(pl->d_w_comb);
   delete pl;
   return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, "rapro_plan_destroy");
 }

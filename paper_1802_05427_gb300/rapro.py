@@ -21,6 +21,7 @@ RAPRO_OK, RAPRO_ERR_INVALID_ARG, RAPRO_ERR_CUDA, RAPRO_ERR_NOT_POSDEF = 0, 1, 2,
 RAPRO_ERR_TIMEOUT, RAPRO_ERR_UNSUPPORTED, RAPRO_ERR_NOMEM = 4, 5, 6
 RAPRO_PILOT_ORTHOGONAL, RAPRO_PILOT_COMB = 0, 1
 RAPRO_PDP_EXP, RAPRO_PDP_UNIFORM_L = 0, 1
+RAPRO_COMB_3W, RAPRO_COMB_SW, RAPRO_COMB_INTERP3 = 0, 1, 2
 RAPRO_MAX_PILOT_SYM = 8
 
 
@@ -32,6 +33,7 @@ class RaproParams(ctypes.Structure):
         ("pilot_layout", ctypes.c_int), ("subblock", ctypes.c_int), ("sigma2", ctypes.c_double),
         ("pdp", ctypes.c_int), ("n_taps", ctypes.c_int), ("tau_rms", ctypes.c_double),
         ("L", ctypes.c_double), ("qam_bits", ctypes.c_int),
+        ("comb_spacing", ctypes.c_int), ("comb_method", ctypes.c_int),
     ]
 
 
@@ -58,6 +60,8 @@ def lib() -> ctypes.CDLL:
         "rapro_last_error": ([], ctypes.c_char_p),
         "rapro_params_validate": ([ctypes.POINTER(RaproParams)], ctypes.c_int),
         "rapro_build_weights_host": ([ctypes.POINTER(RaproParams), ctypes.c_int, _P], ctypes.c_int),
+        "rapro_build_comb_weights_host": ([ctypes.POINTER(RaproParams), _P], ctypes.c_int),
+        "rapro_ce_comb": ([_P, _P, _P, _P, _P], ctypes.c_int),
         "rapro_plan_create": ([ctypes.POINTER(RaproParams), ctypes.POINTER(_P)], ctypes.c_int),
         "rapro_plan_destroy": ([_P], ctypes.c_int),
         "rapro_plan_dims": ([_P, _P, _P, _P, _P], ctypes.c_int),
@@ -94,7 +98,8 @@ def make_params(*, M: int, K: int, n_sc: int, n_fft: int, subblock: int, sigma2:
                 qam_bits: int, n_sym: int = 14, n_pilot_sym: int = 2,
                 pilot_sym_idx: Optional[Sequence[int]] = None, pdp: int = RAPRO_PDP_EXP,
                 n_taps: int = 6, tau_rms: float = 4.0, L: float = 8.0,
-                pilot_layout: int = RAPRO_PILOT_ORTHOGONAL) -> RaproParams:
+                pilot_layout: int = RAPRO_PILOT_ORTHOGONAL, comb_spacing: int = 0,
+                comb_method: int = RAPRO_COMB_SW) -> RaproParams:
     """Build a rapro_params; by default each slot's pilot sits in its 4th symbol (3, 10)."""
     p = RaproParams()
     p.M, p.K, p.n_sc, p.n_fft = M, K, n_sc, n_fft
@@ -106,6 +111,7 @@ def make_params(*, M: int, K: int, n_sc: int, n_fft: int, subblock: int, sigma2:
         p.pilot_sym_idx[j] = v
     p.pilot_layout, p.subblock, p.sigma2 = pilot_layout, subblock, sigma2
     p.pdp, p.n_taps, p.tau_rms, p.L, p.qam_bits = pdp, n_taps, tau_rms, L, qam_bits
+    p.comb_spacing, p.comb_method = comb_spacing, comb_method
     return p
 
 
@@ -120,6 +126,16 @@ def rapro_build_weights_host(p: RaproParams, block_len: int):
     _check(lib().rapro_build_weights_host(ctypes.byref(p), block_len, buf.ctypes.data),
            "rapro_build_weights_host")
     return (buf[0::2] + 1j * buf[1::2]).reshape(block_len, block_len)
+
+
+def rapro_build_comb_weights_host(p: RaproParams):
+    """FP64 comb weights (numpy complex128 [sets][Q][Q][Q]: set, weight index, row, column)."""
+    import numpy as np
+    Q = p.comb_spacing if p.comb_method == RAPRO_COMB_SW else 3
+    sets = p.K if p.comb_method == RAPRO_COMB_SW else 1
+    buf = np.zeros(2 * sets * Q ** 3, dtype=np.float64)
+    _check(lib().rapro_build_comb_weights_host(ctypes.byref(p), buf.ctypes.data), "rapro_build_comb_weights_host")
+    return (buf[0::2] + 1j * buf[1::2]).reshape(sets, Q, Q, Q)
 
 
 class Plan:
@@ -162,7 +178,9 @@ class Plan:
     def shapes(self) -> dict:
         p = self.params
         T, D, K, M, N, q = self.T, self.D, p.K, p.M, p.n_sc, p.qam_bits
-        return dict(y_pilot=(T, K, M, N), pilots=(T, K, N), y_data=(T * D, M, N), h=(T, K, M, N),
+        comb = p.pilot_layout == RAPRO_PILOT_COMB
+        return dict(y_pilot=(T, M, N) if comb else (T, K, M, N), pilots=(T, N) if comb else (T, K, N),
+                    y_data=(T * D, M, N), h=(T, K, M, N),
                     x_eq=(T * D, K, N), labels=(T * D, K, N), llr=(T * D, K, N, q), info=(T, N))
 
 
@@ -223,6 +241,15 @@ def rapro_ce_ls_lmmse(plan: Plan, y_pilot, pilots, h, w_override=None, stream=No
     _check(lib().rapro_ce_ls_lmmse(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
                                    _ptr(pilots, s["pilots"], c64, "pilots"), _w_override(plan, w_override),
                                    _ptr(h, s["h"], c64, "h"), _stream(stream)), "rapro_ce_ls_lmmse")
+
+
+def rapro_ce_comb(plan: Plan, y_pilot, pilots, h, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    _check(lib().rapro_ce_comb(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
+                               _ptr(pilots, s["pilots"], c64, "pilots"), _ptr(h, s["h"], c64, "h"),
+                               _stream(stream)), "rapro_ce_comb")
 
 
 def rapro_mmse_detect(plan: Plan, h, y_data, x_eq, labels=None, llr=None, info=None, stream=None) -> None:

@@ -49,7 +49,7 @@ def _good():
     ("n_taps", 0, R.RAPRO_ERR_INVALID_ARG), ("tau_rms", 0.0, R.RAPRO_ERR_INVALID_ARG),
     ("pdp", 7, R.RAPRO_ERR_INVALID_ARG), ("n_sym", 15, R.RAPRO_ERR_INVALID_ARG),
     ("n_sym", 30, R.RAPRO_ERR_INVALID_ARG), ("n_pilot_sym", 0, R.RAPRO_ERR_INVALID_ARG),
-    ("pilot_layout", R.RAPRO_PILOT_COMB, R.RAPRO_ERR_UNSUPPORTED),
+    ("pilot_layout", 7, R.RAPRO_ERR_INVALID_ARG),
 ])
 def test_params_validation(lib, field, value, expect):
     p = _good()
@@ -81,3 +81,55 @@ def test_host_fp64_weights_match_oracle(lib, B, pdp):
 def test_host_weights_reject_bad_block(lib):
     with pytest.raises(R.RaproError):
         R.rapro_build_weights_host(_good(), 0)
+
+
+# ------------------------------------------------------------------ comb layout
+def _comb(method=R.RAPRO_COMB_SW, S=12, sh=synth.PAPER_SCALE, pdp="exp"):
+    p = params_for(sh, 1, pdp=pdp)
+    p.pilot_layout, p.comb_spacing, p.comb_method = R.RAPRO_PILOT_COMB, S, method
+    p.subblock = 0                                    # unused by comb plans
+    return p
+
+
+@pytest.mark.parametrize("field,value", [
+    ("comb_spacing", 11), ("comb_spacing", 17), ("comb_spacing", 7), ("comb_method", 5), ("n_sc", 132),
+])
+def test_comb_params_validation(lib, field, value):
+    """K <= S <= 16, S | n_sc, enough tones for the window, a known method."""
+    p = _comb()
+    assert R.rapro_params_validate(p) == R.RAPRO_OK
+    setattr(p, field, value)
+    assert R.rapro_params_validate(p) == R.RAPRO_ERR_INVALID_ARG
+    assert lib.rapro_last_error().decode()
+
+
+def test_comb_3w_needs_three_dividing_the_spacing(lib):
+    p = _comb(R.RAPRO_COMB_3W, S=16)
+    assert R.rapro_params_validate(p) == R.RAPRO_ERR_INVALID_ARG
+    p = _comb(R.RAPRO_COMB_INTERP3, S=12)
+    assert R.rapro_params_validate(p) == R.RAPRO_OK
+
+
+@pytest.mark.parametrize("method", [R.RAPRO_COMB_3W, R.RAPRO_COMB_SW])
+@pytest.mark.parametrize("pdp", ["exp", "uniform_L"])
+def test_host_comb_weights_match_oracle(lib, method, pdp):
+    """The library's FP64 comb weights (Cholesky) equal the oracle's per-group W (LU), for
+    every weight index and user, mapped through the oracle's group tables."""
+    sh = synth.PAPER_SCALE
+    S, N = 12, sh.n_sc
+    p = _comb(method, S, pdp=pdp)
+    W = R.rapro_build_comb_weights_host(p)
+    r = oracle_r(sh, pdp)
+    om = O.COMB_SW if method == R.RAPRO_COMB_SW else O.COMB_3W
+    Q = S if method == R.RAPRO_COMB_SW else 3
+    for k in range(sh.K):
+        tones = O.comb_tones(k, S, N)
+        seen = set()
+        for o, i0, widx in O.comb_groups(om, k, S, N):
+            if widx in seen:
+                continue
+            seen.add(widx)
+            Wo = O.comb_weight(o, tones[i0:i0 + Q], r, sh.sigma2)
+            got = W[k if method == R.RAPRO_COMB_SW else 0, widx]
+            np.testing.assert_allclose(got, Wo, rtol=0, atol=1e-10 * max(1.0, np.abs(Wo).max()))
+        assert seen == set(range(Q))

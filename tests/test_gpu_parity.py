@@ -307,3 +307,83 @@ def test_invalid_pointers_are_rejected_without_launch():
     assert lib.rapro_ce_lmmse_subblock(plan.handle, x.data_ptr(), None, x.data_ptr(), None) == \
         R.RAPRO_ERR_INVALID_ARG
     assert plan.device_status() == 0
+
+
+# ------------------------------------------------------- comb pilots (Sec. II, IV-B)
+COMB_METHODS = {R.RAPRO_COMB_3W: O.COMB_3W, R.RAPRO_COMB_SW: O.COMB_SW, R.RAPRO_COMB_INTERP3: O.COMB_INTERP3}
+COMB_CASES = [
+    # name, shape, comb spacing S
+    ("tiny", synth.SubframeShape(M=8, K=2, n_sc=72, n_fft=128, qam_bits=2), 6),
+    ("ragged_antennas", synth.SubframeShape(M=13, K=4, n_sc=96, n_fft=128, n_taps=5, tau_rms=3.0, qam_bits=2), 6),
+    ("spacing15", synth.SubframeShape(M=5, K=3, n_sc=240, n_fft=512, qam_bits=4), 15),
+    ("paper_scale", synth.PAPER_SCALE, 12),
+]
+
+
+def comb_params(sh, S, method):
+    p = params_for(sh, 1)
+    p.pilot_layout, p.comb_spacing, p.comb_method, p.subblock = R.RAPRO_PILOT_COMB, S, method, 0
+    return p
+
+
+def oracle_comb_h(sh, c64, S, method):
+    h_ls = O.comb_ls(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128), sh.K, S)
+    if method == R.RAPRO_COMB_INTERP3:
+        return O.comb_interp3_ls(h_ls, S, sh.n_sc)
+    return O.comb_lmmse(h_ls, COMB_METHODS[method], S, sh.n_sc, oracle_r(sh), sh.sigma2)
+
+
+@pytest.mark.parametrize("method", list(COMB_METHODS), ids=["3W", "SW", "interp3"])
+@pytest.mark.parametrize("name,sh,S", COMB_CASES, ids=[c[0] for c in COMB_CASES])
+def test_comb_estimate_parity(name, sh, S, method):
+    """rapro_ce_comb against the oracle: LS on each user's tones, the groups of Tables I-II
+    with their weights, interpolation and zero-order hold, for every user and subcarrier."""
+    sf = synth.make_comb_subframe(sh, seed=synth.SEED_BASE + 30, S=S)
+    c64 = {k: synth.as_c64(sf[k]) for k in ("y_pilot", "pilots", "y_data")}
+    plan = R.Plan(comb_params(sh, S, method))
+    h = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
+    R.rapro_ce_comb(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), h)
+    ref = oracle_comb_h(sh, c64, S, method)
+    e = rel_err_per(_host(h), ref, axes=(2, 3))
+    assert e.max() <= TOL, e.max()
+
+
+@pytest.mark.parametrize("method", list(COMB_METHODS), ids=["3W", "SW", "interp3"])
+def test_comb_receive_subframe_parity(method):
+    """The whole comb-pilot receive (estimate, then the MMSE detector) against the oracle."""
+    sh = synth.SubframeShape(M=32, K=8, n_sc=600, n_fft=1024, n_taps=6, tau_rms=3.0, snr_db=18.0, qam_bits=4)
+    S = 12
+    sf = synth.make_comb_subframe(sh, seed=synth.SEED_BASE + 31, S=S)
+    c64 = {k: synth.as_c64(sf[k]) for k in ("y_pilot", "pilots", "y_data")}
+    plan = R.Plan(comb_params(sh, S, method))
+    s = plan.shapes()
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+    lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
+    llr = torch.empty(s["llr"], dtype=torch.float32, device="cuda")
+    info = torch.full(s["info"], -7, dtype=torch.int32, device="cuda")
+    h = torch.empty(s["h"], dtype=torch.complex64, device="cuda")
+    R.rapro_receive_subframe(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"]), x, lab, llr,
+                             info, h_out=h)
+    o = O.comb_receive_subframe(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128),
+                                c64["y_data"].astype(np.complex128), K=sh.K, S=S, method=COMB_METHODS[method],
+                                sigma2=sh.sigma2, r=oracle_r(sh), n_data_per_slot=sh.n_data_per_slot,
+                                q=sh.qam_bits)
+    assert rel_err_per(_host(h), o["h"], axes=(2, 3)).max() <= TOL
+    assert (_host(info) == 0).all()
+    check_detection(dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr)), o, sh.qam_bits)
+
+
+def test_comb_and_orthogonal_plans_reject_each_others_estimators():
+    sh = synth.TINY
+    comb = R.Plan(comb_params(sh, 6, R.RAPRO_COMB_SW))
+    orth = R.Plan(params_for(sh, 12))
+    sc, so = comb.shapes(), orth.shapes()
+    h = torch.empty(sc["h"], dtype=torch.complex64, device="cuda")
+    with pytest.raises(R.RaproError) as e:
+        R.rapro_ce_ls_lmmse(comb, torch.zeros(sc["y_pilot"], dtype=torch.complex64, device="cuda"),
+                            torch.zeros(sc["pilots"], dtype=torch.complex64, device="cuda"), h)
+    assert e.value.status == R.RAPRO_ERR_UNSUPPORTED
+    with pytest.raises(R.RaproError) as e:
+        R.rapro_ce_comb(orth, torch.zeros(so["y_pilot"], dtype=torch.complex64, device="cuda"),
+                        torch.zeros(so["pilots"], dtype=torch.complex64, device="cuda"), h)
+    assert e.value.status == R.RAPRO_ERR_UNSUPPORTED
