@@ -475,6 +475,55 @@ def run_rapro(args):
                 torch.cuda.synchronize()
                 sweep[str(Bs)] = res_per_step * r2 * GRAPH_STEPS / (e0.elapsed_time(e1) * 1e-3)
 
+    # comb pilots (Sec. II, IV-B) on the same 128 x 12 x 1200 shape: 12W, 3W, interpolated LS
+    comb = {}
+    if not args.no_sweep and rank == 0 and world == 1:
+        S = 12
+        csets = []
+        for i in range(N_SETS):
+            sf = synth.make_comb_subframe(sh, seed=synth.SEED_BASE + 2000 + i, S=S)
+            csets.append({k: torch.from_numpy(synth.as_c64(sf[k])).to(dev) for k in ("y_pilot", "pilots", "y_data")})
+        for mname, method in (("12W", R.RAPRO_COMB_SW), ("3W", R.RAPRO_COMB_3W), ("interp3_ls", R.RAPRO_COMB_INTERP3)):
+            pc = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=0, sigma2=sh.sigma2,
+                               qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms,
+                               pilot_layout=R.RAPRO_PILOT_COMB, comb_spacing=S, comb_method=method)
+            with R.Plan(pc) as plc:
+                def cstep(i, det=True, stream=None):
+                    d, o = csets[i % N_SETS], outs[i % IN_FLIGHT]
+                    R.rapro_ce_comb(plc, d["y_pilot"], d["pilots"], o["h"], stream=stream)
+                    if det:
+                        R.rapro_mmse_detect(plc, o["h"], d["y_data"], o["x"], o["lab"], None, o["info"], stream=stream)
+
+                def ccapture(det, pipelines):
+                    g = torch.cuda.CUDAGraph()
+                    st = torch.cuda.Stream()
+                    side = [torch.cuda.Stream() for _ in range(pipelines)]
+                    st.wait_stream(torch.cuda.current_stream())
+                    with torch.cuda.stream(st):
+                        with torch.cuda.graph(g, stream=st):
+                            fork = torch.cuda.Event()
+                            fork.record(st)
+                            for q in side:
+                                q.wait_event(fork)
+                            for i in range(GRAPH_STEPS):
+                                cstep(i, det, stream=side[i % pipelines])
+                            for q in side:
+                                join = torch.cuda.Event()
+                                join.record(q)
+                                st.wait_event(join)
+                    torch.cuda.synchronize()
+                    return g
+                for i in range(3):
+                    cstep(i)
+                torch.cuda.synchronize()
+                gc_full, gc_est = ccapture(True, IN_FLIGHT), ccapture(False, 1)
+                us_full = time_graph(gc_full, 64)
+                us_c = time_graph(gc_est, 64)
+                cb = 8 * (sh.n_slots * sh.M * sh.n_sc + sh.n_slots * sh.n_sc + sh.n_slots * sh.K * sh.M * sh.n_sc)
+                comb[mname] = {"res_per_s": res_per_step / (us_full * 1e-6), "estimator_us": us_c,
+                               "estimator_alg_bytes": cb, "estimator_hbm_frac": cb / (us_c * 1e-6) / (peaks()[0] * 1e9)}
+                assert plc.device_status() == 0
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -514,7 +563,8 @@ def run_rapro(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "Receiver.receive_host (pinned host in/out, rapro_receive_subframe)"},
             "gpu_launches": 2 * args.steps, "clocks": clk,
-            "kernels": rows, "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K}
+            "kernels": rows, "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K,
+            "comb_pilots": comb}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -48,9 +48,13 @@ __global__ void __launch_bounds__(COMB_THREADS) comb_kernel(const CombArgs a) {
   float2* ls = sm + nw;                  // [COMB_ROWS][P]
   const float2* wsrc = a.w + (METHOD == RAPRO_COMB_SW ? size_t(k) * nw : 0);
   for (int e = threadIdx.x; e < nw; e += blockDim.x) ws[e] = wsrc[e];
-  // Eq. 9 on user k's tones n = k + iS: y conj(p) / |p|^2.
-  for (int e = threadIdx.x; e < rows * P; e += blockDim.x) {
+  // Eq. 9 on user k's tones n = k + iS: y conj(p) / |p|^2 (rows past the last antenna: 0).
+  for (int e = threadIdx.x; e < COMB_ROWS * P; e += blockDim.x) {
     const int r = e / P, i = e - r * P;
+    if (r >= rows) {
+      ls[e] = make_float2(0.f, 0.f);
+      continue;
+    }
     const int n = k + i * S;
     const float2 yv = a.y[(size_t(t) * a.M + m0 + r) * N + n];
     const float2 pv = a.pil[size_t(t) * N + n];
@@ -68,16 +72,20 @@ __global__ void __launch_bounds__(COMB_THREADS) comb_kernel(const CombArgs a) {
       float2 wv[QMAX];
 #pragma unroll
       for (int i = 0; i < QMAX; ++i) wv[i] = i < S ? wr[i] : make_float2(0.f, 0.f);
-#pragma unroll 2
-      for (int r = 0; r < COMB_ROWS; ++r) {
-        if (r >= rows) break;
-        const float2* x = ls + r * P + i0;
-        float2 acc = make_float2(0.f, 0.f);
+      // All staged rows at once: COMB_ROWS independent accumulation chains (rows past the
+      // last antenna are zero and not stored).
+      float2 acc[COMB_ROWS];
 #pragma unroll
-        for (int i = 0; i < QMAX; ++i)
-          if (i < S) cmac(acc, wv[i], x[i]);
-        hout[size_t(r) * N + n] = acc;
-      }
+      for (int r = 0; r < COMB_ROWS; ++r) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < QMAX; ++i)
+        if (i < S) {
+#pragma unroll
+          for (int r = 0; r < COMB_ROWS; ++r) cmac(acc[r], wv[i], ls[r * P + i0 + i]);
+        }
+#pragma unroll
+      for (int r = 0; r < COMB_ROWS; ++r)
+        if (r < rows) hout[size_t(r) * N + n] = acc[r];
     } else {
       // Zero-order hold onto the 3W positions k + v S/3 (v = 3j + u): the last one <= n,
       // the first one before the user's first tone.
