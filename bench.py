@@ -475,6 +475,45 @@ def run_rapro(args):
                 torch.cuda.synchronize()
                 sweep[str(Bs)] = res_per_step * r2 * GRAPH_STEPS / (e0.elapsed_time(e1) * 1e-3)
 
+    # precision form: the sub-block filter as one BF16 pass on the tensor cores
+    prec = {}
+    if not args.no_sweep and rank == 0 and world == 1 and B % 2 == 0 and B <= 16 and sh.n_sc % B == 0:
+        pb = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, sigma2=sh.sigma2,
+                           qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms, precision=R.RAPRO_PREC_BF16)
+        with R.Plan(pb) as plb:
+            def bstep(i, det=True, stream=None):
+                d, o = sets[i % N_SETS], outs[i % IN_FLIGHT]
+                R.rapro_ce_ls_lmmse(plb, d["y_pilot"], d["pilots"], o["h"], stream=stream)
+                if det:
+                    R.rapro_mmse_detect(plb, o["h"], d["y_data"], o["x"], o["lab"], None, o["info"], stream=stream)
+            for i in range(3):
+                bstep(i)
+            torch.cuda.synchronize()
+            gb = []
+            for det, pipes in ((True, IN_FLIGHT), (False, 1)):
+                g = torch.cuda.CUDAGraph()
+                st = torch.cuda.Stream()
+                side = [torch.cuda.Stream() for _ in range(pipes)]
+                st.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(st):
+                    with torch.cuda.graph(g, stream=st):
+                        fork = torch.cuda.Event()
+                        fork.record(st)
+                        for q in side:
+                            q.wait_event(fork)
+                        for i in range(GRAPH_STEPS):
+                            bstep(i, det, stream=side[i % pipes])
+                        for q in side:
+                            join = torch.cuda.Event()
+                            join.record(q)
+                            st.wait_event(join)
+                torch.cuda.synchronize()
+                gb.append(g)
+            us_b_full, us_b_est = time_graph(gb[0], 64), time_graph(gb[1], 64)
+            prec["bf16_tc"] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est,
+                               "estimator_hbm_frac": alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)}
+            assert plb.device_status() == 0
+
     # comb pilots (Sec. II, IV-B) on the same 128 x 12 x 1200 shape: 12W, 3W, interpolated LS
     comb = {}
     if not args.no_sweep and rank == 0 and world == 1:
@@ -564,7 +603,7 @@ def run_rapro(args):
                     "api": "Receiver.receive_host (pinned host in/out, rapro_receive_subframe)"},
             "gpu_launches": 2 * args.steps, "clocks": clk,
             "kernels": rows, "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K,
-            "comb_pilots": comb}
+            "comb_pilots": comb, "precision_form": prec}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

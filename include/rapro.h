@@ -97,6 +97,18 @@ typedef enum {
   RAPRO_PDP_UNIFORM_L = 1
 } rapro_pdp_kind;
 
+/* Arithmetic of the sub-block LMMSE filter (Eq. 12). */
+typedef enum {
+  /* FP32 accuracy: TF32 tensor cores with three split passes (even B <= 16 dividing n_sc,
+   * 16-byte aligned arrays) or FP32 FMAs otherwise. */
+  RAPRO_PREC_FP32 = 0,
+  /* Precision form: one BF16 pass on the tensor cores, FP32 accumulation (W and the LS
+   * estimate rounded to BF16; relative filter error ~ 2^-8).  Needs the orthogonal layout,
+   * an even B <= 16 dividing n_sc and 16-byte aligned arrays; rapro_ce_lmmse_subblock and
+   * w_override are not available (RAPRO_ERR_UNSUPPORTED). */
+  RAPRO_PREC_BF16 = 1
+} rapro_precision;
+
 #define RAPRO_MAX_PILOT_SYM 8
 #define RAPRO_MAX_USERS 16       /* K limit of the register-tiled detector */
 #define RAPRO_MAX_DATA_PER_SLOT 12
@@ -123,6 +135,7 @@ typedef struct {
   int comb_spacing;      /* S: tone spacing of each user's comb, K <= S <= 16, S | n_sc,
                             P = n_sc / S tones per user, 2 <= P <= 1024, P >= the window */
   int comb_method;       /* rapro_comb_method */
+  int precision;         /* rapro_precision of the sub-block filter, default RAPRO_PREC_FP32 */
 } rapro_params;
 
 typedef struct rapro_plan rapro_plan;

@@ -431,6 +431,7 @@ cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
   const bool override_w = d_w_main != pl.d_w_main;
   if (override_w) return launch_tiled(pl, x, pil, d_w_main, nullptr, 1, out, st);
   if (lmmse_tc_ok(pl, x, pil, out)) return launch_lmmse_tc(pl, x, pil, out, st);
+  if (pl.p.precision == RAPRO_PREC_BF16) return cudaErrorNotSupported;   // never a silent FP32 fallback
   const int B = pl.B;
   if (B <= 4) return launch_small<4>(pl, x, pil, out, st);
   if (B <= 8) return launch_small<8>(pl, x, pil, out, st);

@@ -31,6 +31,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "rapro_internal.h"
 #include "rapro_ptx.cuh"
 
@@ -60,12 +62,29 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint3
 constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TC_N >> 3) << 17) |
                                 (uint32_t(TC_ROWS >> 4) << 24);
 
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = TC_N.
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TC_N >> 3) << 17) |
+                                (uint32_t(TC_ROWS >> 4) << 24);
+
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(kIdescTf32), "r"(accumulate ? 1 : 0)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate ? 1 : 0)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (lower address) = lo
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
@@ -83,18 +102,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 }  // namespace
 
-template <int KR>
-__global__ void __launch_bounds__(TC_THREADS) lmmse_tc_kernel(const float2* __restrict__ y,
+// KR: reals per row-block, 2B padded to the MMA's K step (8 for TF32, 16 for BF16).
+// BF: one BF16 pass (the precision form) instead of the three TF32 passes.
+template <int KR, bool BF>
+__global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* __restrict__ y,
                                                               const float2* __restrict__ pil,
                                                               float2* __restrict__ out, int M, int N, int B,
                                                               long long n_rb, int n_tiles, int* status,
-                                                              const float* __restrict__ w_tc) {
-  static_assert(KR % 8 == 0 && KR <= 32, "2B padded to a multiple of 8, at most 32");
-  constexpr uint32_t SBO = (KR / 4) * 128;                      // 8-row group stride (A and B)
-  constexpr int A_BYTES = TC_ROWS * KR * 4;
-  constexpr int B_BYTES = TC_N * KR * 4;
+                                                              const void* __restrict__ w_tc) {
+  static_assert(KR % (BF ? 16 : 8) == 0 && KR <= 32, "2B padded to the K step, at most 32");
+  constexpr int ELT = BF ? 2 : 4;                               // operand bytes
+  constexpr int CE = 16 / ELT;                                  // operand elements per 16-byte core row
+  constexpr uint32_t SBO = (KR / CE) * 128;                     // 8-row group stride (A and B)
+  constexpr int A_BYTES = TC_ROWS * KR * ELT;
+  constexpr int B_BYTES = TC_N * KR * ELT;
+  constexpr int NA = BF ? 1 : 2;                                // A parts: BF16, or TF32 hi and lo
+  constexpr int KSTEPS = KR / (2 * CE);                         // MMAs of K = 2 core columns (32 bytes)
   constexpr int KQ = KR / 4;                                    // float4 (2 complex) per row-block
   constexpr int KH = KQ / 2;                                    // float4 per consumer thread
+  static_assert(!BF || KH % 2 == 0, "a BF16 core row holds two float4 of reals");
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);           // [TC_STAGES] raw tile landed
   uint64_t* epi = full + TC_STAGES;                             // [TC_STAGES] tile written back
@@ -103,14 +129,12 @@ __global__ void __launch_bounds__(TC_THREADS) lmmse_tc_kernel(const float2* __re
   uint64_t* wbar = done + 2;                                    // weights landed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
   volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  unsigned char* sA = smem + 1024;                              // [2 buffers][hi, lo][A_BYTES]
-  unsigned char* sBh = sA + 4 * A_BYTES;
-  unsigned char* sBl = sBh + B_BYTES;
-  float2* raw = reinterpret_cast<float2*>(sBl + B_BYTES);       // [TC_STAGES][TC_ROWS * B]
+  unsigned char* sA = smem + 1024;                              // [2 buffers][NA parts][A_BYTES]
+  unsigned char* sBh = sA + 2 * NA * A_BYTES;                   // weights (TF32: hi, then lo)
+  float2* raw = reinterpret_cast<float2*>(sBh + NA * B_BYTES);  // [TC_STAGES][TC_ROWS * B]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile_elems = TC_ROWS * B;
   const int nb = N / B;
-  (void)sBl;
 
   if (tid == 0) {
     for (int st = 0; st < TC_STAGES; ++st) {
@@ -159,9 +183,9 @@ __global__ void __launch_bounds__(TC_THREADS) lmmse_tc_kernel(const float2* __re
         mbar_arrive_expect_tx(&full[st], bytes);
         bulk_load(raw + size_t(st) * tile_elems, y + (size_t)tile_of(it) * tile_elems, bytes, &full[st]);
       };
-      // The weights arrive already in the canonical layout (hi, then lo, 2 * B_BYTES).
-      mbar_arrive_expect_tx(wbar, 2 * B_BYTES);
-      bulk_load(sBh, w_tc, 2 * B_BYTES, wbar);
+      // The weights arrive already in the canonical layout (NA * B_BYTES).
+      mbar_arrive_expect_tx(wbar, NA * B_BYTES);
+      bulk_load(sBh, w_tc, NA * B_BYTES, wbar);
       int issued = 0;
       for (; issued < TC_STAGES && issued < my_tiles; ++issued) issue(issued);
       bool bad = false;
@@ -200,17 +224,23 @@ __global__ void __launch_bounds__(TC_THREADS) lmmse_tc_kernel(const float2* __re
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // D[buf] = Ah Wh^T + Ah Wl^T + Al Wh^T over K = KR in steps of 8.
-        const unsigned char* ah = sA + buf * 2 * A_BYTES;
+        // TF32: D[buf] = Ah Wh^T + Ah Wl^T + Al Wh^T;  BF16: D[buf] = A W^T.  K = KR in
+        // steps of two core columns.
+        const unsigned char* ah = sA + buf * NA * A_BYTES;
         const unsigned char* al = ah + A_BYTES;
         const uint32_t d = tmem + uint32_t(buf * TC_N);
 #pragma unroll
-        for (int kg = 0; kg < KR / 8; ++kg) {
-          const uint64_t dah = smem_desc(ah + kg * 256, 128, SBO), dal = smem_desc(al + kg * 256, 128, SBO);
-          const uint64_t dbh = smem_desc(sBh + kg * 256, 128, SBO), dbl = smem_desc(sBh + B_BYTES + kg * 256, 128, SBO);
-          mma_tf32(d, dah, dbh, kg > 0);
-          mma_tf32(d, dah, dbl, true);
-          mma_tf32(d, dal, dbh, true);
+        for (int kg = 0; kg < KSTEPS; ++kg) {
+          const uint64_t dah = smem_desc(ah + kg * 256, 128, SBO), dbh = smem_desc(sBh + kg * 256, 128, SBO);
+          if (BF) {
+            mma_bf16(d, dah, dbh, kg > 0);
+          } else {
+            const uint64_t dal = smem_desc(al + kg * 256, 128, SBO);
+            const uint64_t dbl = smem_desc(sBh + B_BYTES + kg * 256, 128, SBO);
+            mma_tf32(d, dah, dbh, kg > 0);
+            mma_tf32(d, dah, dbl, true);
+            mma_tf32(d, dal, dbh, true);
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&done[buf]))
@@ -240,26 +270,42 @@ __global__ void __launch_bounds__(TC_THREADS) lmmse_tc_kernel(const float2* __re
     };
     // LS estimate (y conj(p) / |p|^2) split into TF32 hi and lo, canonical K-major layout.
     auto ls_split = [&](int it, const float4 (&pv)[KH], int buf) {
-      unsigned char* ah = sA + buf * 2 * A_BYTES;
+      unsigned char* ah = sA + buf * NA * A_BYTES;
       unsigned char* al = ah + A_BYTES;
       const bool live = r < tile_count(it);
       const float4* x4 = reinterpret_cast<const float4*>(raw + size_t(it % TC_STAGES) * tile_elems + r * B);
+      float4 q[KH];
 #pragma unroll
       for (int j = 0; j < KH; ++j) {
         const int kg = half * KH + j;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        q[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (live && 2 * kg < B) {
           const float4 x = x4[kg], p = pv[j];
           const float i0 = __fdividef(1.0f, fmaf(p.x, p.x, p.y * p.y));
           const float i1 = __fdividef(1.0f, fmaf(p.z, p.z, p.w * p.w));
-          q = make_float4(fmaf(x.x, p.x, x.y * p.y) * i0, fmaf(x.y, p.x, -x.x * p.y) * i0,
-                          fmaf(x.z, p.z, x.w * p.w) * i1, fmaf(x.w, p.z, -x.z * p.w) * i1);
+          q[j] = make_float4(fmaf(x.x, p.x, x.y * p.y) * i0, fmaf(x.y, p.x, -x.x * p.y) * i0,
+                             fmaf(x.z, p.z, x.w * p.w) * i1, fmaf(x.w, p.z, -x.z * p.w) * i1);
         }
-        const float4 h = make_float4(tf32_hi(q.x), tf32_hi(q.y), tf32_hi(q.z), tf32_hi(q.w));
-        const float4 l = make_float4(q.x - h.x, q.y - h.y, q.z - h.z, q.w - h.w);
-        const int off = (r / 8) * SBO + kg * 128 + (r % 8) * 16;
-        *reinterpret_cast<float4*>(ah + off) = h;
-        *reinterpret_cast<float4*>(al + off) = l;
+      }
+      if (BF) {
+        // Four complex (8 BF16) per 16-byte core row.
+#pragma unroll
+        for (int j = 0; j < KH; j += 2) {
+          const int c = (half * KH + j) / 2;
+          const uint4 v = make_uint4(pack_bf16x2(q[j].x, q[j].y), pack_bf16x2(q[j].z, q[j].w),
+                                     pack_bf16x2(q[j + 1].x, q[j + 1].y), pack_bf16x2(q[j + 1].z, q[j + 1].w));
+          *reinterpret_cast<uint4*>(ah + (r / 8) * SBO + c * 128 + (r % 8) * 16) = v;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+          const int kg = half * KH + j;
+          const float4 h = make_float4(tf32_hi(q[j].x), tf32_hi(q[j].y), tf32_hi(q[j].z), tf32_hi(q[j].w));
+          const float4 l = make_float4(q[j].x - h.x, q[j].y - h.y, q[j].z - h.z, q[j].w - h.w);
+          const int off = (r / 8) * SBO + kg * 128 + (r % 8) * 16;
+          *reinterpret_cast<float4*>(ah + off) = h;
+          *reinterpret_cast<float4*>(al + off) = l;
+        }
       }
     };
     // Accumulator row r (this warp's quarter of the TMEM lanes) over the raw tile; the
@@ -319,9 +365,10 @@ __global__ void __launch_bounds__(TC_THREADS) lmmse_tc_kernel(const float2* __re
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N) : "memory");
 }
 
-template <int KR>
+template <int KR, bool BF>
 static size_t tc_smem_bytes(int B) {
-  return 1024 + 4 * size_t(TC_ROWS) * KR * 4 + 2 * size_t(TC_N) * KR * 4 +
+  const size_t elt = BF ? 2 : 4, na = BF ? 1 : 2;
+  return 1024 + 2 * na * size_t(TC_ROWS) * KR * elt + na * size_t(TC_N) * KR * elt +
          size_t(TC_STAGES) * TC_ROWS * B * sizeof(float2);
 }
 
@@ -336,9 +383,18 @@ static float tf32_host(float x) {
   return r;
 }
 
-static int kr_for(int B) { return (2 * B + 7) / 8 * 8; }
+static uint16_t bf16_host(float x) {
+  // Round to nearest even at 7 explicit mantissa bits (finite inputs).
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return uint16_t(u >> 16);
+}
 
-template <int KR>
+// Reals per row-block: 2B padded to the K step (8 for TF32, 16 for BF16).
+static int kr_for(int B, bool bf) { return bf ? (2 * B + 15) / 16 * 16 : (2 * B + 7) / 8 * 8; }
+
+template <int KR, bool BF>
 static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
   const int B = pl.B, M = pl.p.M, N = pl.p.n_sc, R = pl.T * pl.p.K * pl.p.M;
   const long long n_rb = (long long)R * (N / B);
@@ -348,26 +404,29 @@ static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  const size_t smem = tc_smem_bytes<KR>(B);
+  const size_t smem = tc_smem_bytes<KR, BF>(B);
   // Resident CTAs per SM: shared memory, threads (2048 per SM) and tensor memory (512 columns).
   int per_sm = int(size_t(smem_sm) / (smem + size_t(reserved)));
   per_sm = std::max(1, std::min({per_sm, 2048 / TC_THREADS, 512 / (2 * TC_N)}));
   const int grid = std::min(n_tiles, per_sm * sms);
-  lmmse_tc_kernel<KR><<<grid, TC_THREADS, smem, st>>>(y, pil, out, M, N, B, n_rb, n_tiles, pl.d_status, pl.d_w_tc);
+  lmmse_tc_kernel<KR, BF><<<grid, TC_THREADS, smem, st>>>(y, pil, out, M, N, B, n_rb, n_tiles, pl.d_status,
+                                                            pl.d_w_tc);
   return cudaGetLastError();
 }
 
 bool lmmse_tc_shape_ok(const Plan& pl) {
+  if (pl.B < 2) return false;
   const long long n_rb = (long long)pl.T * pl.p.K * pl.p.M * (pl.p.n_sc / pl.B);
   return pl.B % 2 == 0 && pl.B <= 16 && pl.tail == 0 && n_rb < (1ll << 31);
 }
 
 // The filter as the MMA's B operand: Wr (TC_N x KR reals, zero padded) in the canonical
-// K-major layout, its TF32 hi part followed by its lo part.
-void build_lmmse_tc_weights(const Plan& pl, std::vector<float>& out) {
-  const int B = pl.B, KR = kr_for(B);
-  const int SBO = (KR / 4) * 128, per = TC_N * KR;
-  out.assign(2 * size_t(per), 0.f);
+// K-major layout: TF32 hi part followed by its lo part, or one BF16 part (as raw bytes).
+void build_lmmse_tc_weights(const Plan& pl, std::vector<unsigned char>& out) {
+  const bool bf = pl.p.precision == RAPRO_PREC_BF16;
+  const int B = pl.B, KR = kr_for(B, bf), elt = bf ? 2 : 4, ce = 16 / elt;
+  const int SBO = (KR / ce) * 128, part = TC_N * KR * elt;
+  out.assign(size_t(bf ? 1 : 2) * part, 0);
   for (int i = 0; i < B; ++i)
     for (int j = 0; j < B; ++j) {
       const float2 v = pl.w_main[size_t(i) * B + j];
@@ -375,10 +434,16 @@ void build_lmmse_tc_weights(const Plan& pl, std::vector<float>& out) {
       for (int a = 0; a < 2; ++a)
         for (int c = 0; c < 2; ++c) {
           const int n = 2 * i + a, k = 2 * j + c;
-          const size_t off = size_t((n / 8) * SBO + (k / 4) * 128 + (n % 8) * 16 + (k % 4) * 4) / 4;
-          const float f = vals[a][c], h = tf32_host(f);
-          out[off] = h;
-          out[per + off] = tf32_host(f - h);
+          const size_t off = size_t((n / 8) * SBO + (k / ce) * 128 + (n % 8) * 16 + (k % ce) * elt);
+          const float f = vals[a][c];
+          if (bf) {
+            const uint16_t h = bf16_host(f);
+            std::memcpy(&out[off], &h, 2);
+          } else {
+            const float h = tf32_host(f), l = tf32_host(f - h);
+            std::memcpy(&out[off], &h, 4);
+            std::memcpy(&out[part + off], &l, 4);
+          }
         }
     }
 }
@@ -390,11 +455,13 @@ bool lmmse_tc_ok(const Plan& pl, const float2* y, const float2* pil, const float
 }
 
 cudaError_t launch_lmmse_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
-  switch (kr_for(pl.B)) {
-    case 8: return launch_tc<8>(pl, y, pil, out, st);
-    case 16: return launch_tc<16>(pl, y, pil, out, st);
-    case 24: return launch_tc<24>(pl, y, pil, out, st);
-    default: return launch_tc<32>(pl, y, pil, out, st);
+  if (pl.p.precision == RAPRO_PREC_BF16)
+    return kr_for(pl.B, true) == 16 ? launch_tc<16, true>(pl, y, pil, out, st) : launch_tc<32, true>(pl, y, pil, out, st);
+  switch (kr_for(pl.B, false)) {
+    case 8: return launch_tc<8, false>(pl, y, pil, out, st);
+    case 16: return launch_tc<16, false>(pl, y, pil, out, st);
+    case 24: return launch_tc<24, false>(pl, y, pil, out, st);
+    default: return launch_tc<32, false>(pl, y, pil, out, st);
   }
 }
 
@@ -404,10 +471,12 @@ cudaError_t prepare_lmmse_tc(int device) {
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   std::call_once(flags[device], [device] {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(lmmse_tc_kernel<8>, A, int(tc_smem_bytes<8>(4)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<16>, A, int(tc_smem_bytes<16>(8)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<24>, A, int(tc_smem_bytes<24>(12)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<32>, A, int(tc_smem_bytes<32>(16)));
+    cudaError_t e = cudaFuncSetAttribute(lmmse_tc_kernel<8, false>, A, int(tc_smem_bytes<8, false>(4)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<16, false>, A, int(tc_smem_bytes<16, false>(8)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<24, false>, A, int(tc_smem_bytes<24, false>(12)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<32, false>, A, int(tc_smem_bytes<32, false>(16)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<16, true>, A, int(tc_smem_bytes<16, true>(8)));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<32, true>, A, int(tc_smem_bytes<32, true>(16)));
     result[device] = e;
   });
   return result[device];

@@ -1,6 +1,7 @@
 // extern "C" entry points: argument checks, then the kernel launchers.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <string>
 
 #include "rapro_internal.h"
@@ -33,6 +34,22 @@ rapro_status orthogonal_only(const Plan* pl) {
   return RAPRO_ERR_UNSUPPORTED;
 }
 
+// The BF16 form runs only on the tensor-core estimator: LS fused, the plan's weights, aligned arrays.
+rapro_status bf16_check(const Plan* pl, const void* y, const void* pil, const void* h, const void* w_override) {
+  if (pl->p.precision != RAPRO_PREC_BF16) return RAPRO_OK;
+  if (!pil || w_override) {
+    set_error("the BF16 form needs the fused LS (pilots) and the plan's weights");
+    return RAPRO_ERR_UNSUPPORTED;
+  }
+  const uintptr_t a = reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(pil) |
+                      reinterpret_cast<uintptr_t>(h);
+  if (a & 15) {
+    set_error("the BF16 form needs 16-byte aligned y_pilot, pilots and h");
+    return RAPRO_ERR_INVALID_ARG;
+  }
+  return RAPRO_OK;
+}
+
 inline const float2* f2(const rapro_c32* p) { return reinterpret_cast<const float2*>(p); }
 inline float2* f2(rapro_c32* p) { return reinterpret_cast<float2*>(p); }
 inline cudaStream_t cs(rapro_stream s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -61,6 +78,7 @@ rapro_status rapro_ce_lmmse_subblock(const rapro_plan* plan, const rapro_c32* h_
   const Plan* pl = reinterpret_cast<const Plan*>(plan);
   rapro_status s = check_device(pl);
   if (s == RAPRO_OK) s = orthogonal_only(pl);
+  if (s == RAPRO_OK) s = bf16_check(pl, h_ls, nullptr, h, w_override);
   if (s != RAPRO_OK) return s;
   const float2* w = w_override ? f2(w_override) : pl->d_w_main;
   return launched(launch_lmmse(*pl, f2(h_ls), nullptr, w, pl->d_w_tail, pl->w_main.data(),
@@ -76,6 +94,7 @@ rapro_status rapro_ce_ls_lmmse(const rapro_plan* plan, const rapro_c32* y_pilot,
   const Plan* pl = reinterpret_cast<const Plan*>(plan);
   rapro_status s = check_device(pl);
   if (s == RAPRO_OK) s = orthogonal_only(pl);
+  if (s == RAPRO_OK) s = bf16_check(pl, y_pilot, pilots, h, w_override);
   if (s != RAPRO_OK) return s;
   const float2* w = w_override ? f2(w_override) : pl->d_w_main;
   return launched(launch_lmmse(*pl, f2(y_pilot), f2(pilots), w, pl->d_w_tail, pl->w_main.data(),
@@ -120,6 +139,7 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
   rapro_status s = check_device(pl);
   if (s != RAPRO_OK) return s;
   float2* h = h_out ? f2(h_out) : pl->d_h_work;
+  if ((s = bf16_check(pl, y_pilot, pilots, h, nullptr)) != RAPRO_OK) return s;
   cudaError_t e = pl->comb ? launch_comb(*pl, f2(y_pilot), f2(pilots), h, cs(stream))
                            : launch_lmmse(*pl, f2(y_pilot), f2(pilots), pl->d_w_main, pl->d_w_tail,
                                           pl->w_main.data(), pl->w_tail.data(), h, cs(stream));

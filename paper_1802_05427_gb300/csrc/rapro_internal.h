@@ -47,7 +47,7 @@ struct Plan {
   float2* d_w_tail = nullptr;
   float2* d_h_work = nullptr;      // [T][K][M][n_sc] estimate workspace
   int* d_status = nullptr;         // device status word
-  float* d_w_tc = nullptr;         // tensor-core filter operand (canonical layout, hi then lo), or null
+  void* d_w_tc = nullptr;          // tensor-core filter operand (canonical layout), or null
   bool comb = false;               // comb pilot layout (Sec. II)
   std::vector<float2> w_comb;      // comb weights [sets][Q][Q][Q] (3W: 1 set, S-W: K sets)
   float2* d_w_comb = nullptr;
@@ -87,7 +87,7 @@ cudaError_t prepare_estimate(int device);
 cudaError_t prepare_lmmse_tc(int device);
 // Tensor-core LS + LMMSE (even B <= 16 dividing n_sc, aligned arrays).
 bool lmmse_tc_shape_ok(const Plan& pl);
-void build_lmmse_tc_weights(const Plan& pl, std::vector<float>& out);
+void build_lmmse_tc_weights(const Plan& pl, std::vector<unsigned char>& out);
 bool lmmse_tc_ok(const Plan& pl, const float2* y, const float2* pil, const float2* out);
 cudaError_t launch_lmmse_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st);
 

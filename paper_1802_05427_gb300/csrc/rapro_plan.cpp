@@ -258,6 +258,15 @@ rapro_status rapro_params_validate(const rapro_params* p) {
     return invalid("unknown pdp kind");
   }
   if (p->qam_bits != 2 && p->qam_bits != 4 && p->qam_bits != 6) return invalid("qam_bits must be 2, 4 or 6");
+  if (p->precision == RAPRO_PREC_BF16) {
+    if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL || p->subblock % 2 != 0 || p->subblock > 16 ||
+        p->n_sc % p->subblock != 0) {
+      set_error("the BF16 form filters on the tensor cores: orthogonal pilots, even subblock <= 16 dividing n_sc");
+      return RAPRO_ERR_UNSUPPORTED;
+    }
+  } else if (p->precision != RAPRO_PREC_FP32) {
+    return invalid("unknown precision");
+  }
   const double elems = double(p->n_pilot_sym) * p->K * p->M * p->n_sc;
   if (elems > 2147483647.0) return invalid("T*K*M*n_sc must fit in int32");
   return RAPRO_OK;
@@ -371,10 +380,10 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
                                   cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W tail");
   if ((e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset status");
   if (!pl->comb && lmmse_tc_shape_ok(*pl)) {
-    std::vector<float> wtc;
+    std::vector<unsigned char> wtc;
     build_lmmse_tc_weights(*pl, wtc);
-    if ((e = cudaMalloc(&pl->d_w_tc, wtc.size() * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc W (tensor cores)");
-    if ((e = cudaMemcpy(pl->d_w_tc, wtc.data(), wtc.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMalloc(&pl->d_w_tc, wtc.size())) != cudaSuccess) return fail(e, "cudaMalloc W (tensor cores)");
+    if ((e = cudaMemcpy(pl->d_w_tc, wtc.data(), wtc.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(e, "cudaMemcpy W (tensor cores)");
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan upload");

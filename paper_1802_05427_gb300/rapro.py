@@ -22,6 +22,7 @@ RAPRO_ERR_TIMEOUT, RAPRO_ERR_UNSUPPORTED, RAPRO_ERR_NOMEM = 4, 5, 6
 RAPRO_PILOT_ORTHOGONAL, RAPRO_PILOT_COMB = 0, 1
 RAPRO_PDP_EXP, RAPRO_PDP_UNIFORM_L = 0, 1
 RAPRO_COMB_3W, RAPRO_COMB_SW, RAPRO_COMB_INTERP3 = 0, 1, 2
+RAPRO_PREC_FP32, RAPRO_PREC_BF16 = 0, 1
 RAPRO_MAX_PILOT_SYM = 8
 
 
@@ -33,7 +34,7 @@ class RaproParams(ctypes.Structure):
         ("pilot_layout", ctypes.c_int), ("subblock", ctypes.c_int), ("sigma2", ctypes.c_double),
         ("pdp", ctypes.c_int), ("n_taps", ctypes.c_int), ("tau_rms", ctypes.c_double),
         ("L", ctypes.c_double), ("qam_bits", ctypes.c_int),
-        ("comb_spacing", ctypes.c_int), ("comb_method", ctypes.c_int),
+        ("comb_spacing", ctypes.c_int), ("comb_method", ctypes.c_int), ("precision", ctypes.c_int),
     ]
 
 
@@ -99,7 +100,7 @@ def make_params(*, M: int, K: int, n_sc: int, n_fft: int, subblock: int, sigma2:
                 pilot_sym_idx: Optional[Sequence[int]] = None, pdp: int = RAPRO_PDP_EXP,
                 n_taps: int = 6, tau_rms: float = 4.0, L: float = 8.0,
                 pilot_layout: int = RAPRO_PILOT_ORTHOGONAL, comb_spacing: int = 0,
-                comb_method: int = RAPRO_COMB_SW) -> RaproParams:
+                comb_method: int = RAPRO_COMB_SW, precision: int = RAPRO_PREC_FP32) -> RaproParams:
     """Build a rapro_params; by default each slot's pilot sits in its 4th symbol (3, 10)."""
     p = RaproParams()
     p.M, p.K, p.n_sc, p.n_fft = M, K, n_sc, n_fft
@@ -111,7 +112,7 @@ def make_params(*, M: int, K: int, n_sc: int, n_fft: int, subblock: int, sigma2:
         p.pilot_sym_idx[j] = v
     p.pilot_layout, p.subblock, p.sigma2 = pilot_layout, subblock, sigma2
     p.pdp, p.n_taps, p.tau_rms, p.L, p.qam_bits = pdp, n_taps, tau_rms, L, qam_bits
-    p.comb_spacing, p.comb_method = comb_spacing, comb_method
+    p.comb_spacing, p.comb_method, p.precision = comb_spacing, comb_method, precision
     return p
 
 

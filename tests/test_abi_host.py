@@ -133,3 +133,15 @@ def test_host_comb_weights_match_oracle(lib, method, pdp):
             got = W[k if method == R.RAPRO_COMB_SW else 0, widx]
             np.testing.assert_allclose(got, Wo, rtol=0, atol=1e-10 * max(1.0, np.abs(Wo).max()))
         assert seen == set(range(Q))
+
+
+# ------------------------------------------------------------- precision form
+def test_precision_validation(lib):
+    p = params_for(synth.PAPER_SCALE, 12)
+    p.precision = R.RAPRO_PREC_BF16
+    assert R.rapro_params_validate(p) == R.RAPRO_OK
+    for B in (7, 48, 13):                  # odd, > 16, not dividing 1200
+        p.subblock = B
+        assert R.rapro_params_validate(p) == R.RAPRO_ERR_UNSUPPORTED
+    p.subblock, p.precision = 12, 5
+    assert R.rapro_params_validate(p) == R.RAPRO_ERR_INVALID_ARG

@@ -387,3 +387,61 @@ def test_comb_and_orthogonal_plans_reject_each_others_estimators():
         R.rapro_ce_comb(orth, torch.zeros(so["y_pilot"], dtype=torch.complex64, device="cuda"),
                         torch.zeros(so["pilots"], dtype=torch.complex64, device="cuda"), h)
     assert e.value.status == R.RAPRO_ERR_UNSUPPORTED
+
+
+# --------------------------------------------- precision form (BF16 tensor cores)
+# One BF16 pass rounds the LS estimate and W to 8 significant bits (unit roundoff 2^-9
+# each) and accumulates in FP32: per output |err| <= sum_j |W_ij| |x_j| (2^-8 + 2^-16), so
+# norm-wise about 2^-8 / sqrt(3) for random signs; the bound below is 2^-7.
+TOL_BF16 = 2.0 ** -7
+
+
+@pytest.mark.parametrize("case", [(8, 2, 72, 128, 12), (5, 3, 100, 256, 10), (6, 2, 96, 128, 16),
+                                  (2, 1, 64, 128, 2), (128, 12, 1200, 2048, 12)])
+def test_bf16_estimator_parity(case):
+    M, K, N, nfft, B = case
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=24 if nfft >= 2048 else 6,
+                             tau_rms=8.0 if nfft >= 2048 else 4.0, snr_db=10.0, qam_bits=2)
+    sf, c64 = _inputs(sh, 5)
+    p = params_for(sh, B)
+    p.precision = R.RAPRO_PREC_BF16
+    plan = R.Plan(p)
+    h = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
+    R.rapro_ce_ls_lmmse(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), h)
+    h_ls = O.ls_estimate(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128))
+    ref = O.subblock_lmmse(h_ls, B, oracle_r(sh), sh.sigma2)
+    e = rel_err_per(_host(h), ref, axes=(2, 3))
+    assert e.max() <= TOL_BF16, e.max()
+    assert e.max() > 1e-5                  # it really is the single BF16 pass
+    with pytest.raises(R.RaproError):
+        R.rapro_ce_lmmse_subblock(plan, _dev(synth.as_c64(h_ls)), h)
+
+
+def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db():
+    """Precision form on the paper-scale shape (64-QAM, 25 dB, several subframes): channel
+    NMSE and post-detection EVM within 0.1 dB of the FP64 oracle's."""
+    sh = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "snr_db": 25.0, "qam_bits": 6})
+    p = params_for(sh, 12)
+    p.precision = R.RAPRO_PREC_BF16
+    plan = R.Plan(p)
+    s = plan.shapes()
+    err_h = err_h_o = pow_h = err_x = err_x_o = pow_x = 0.0
+    for i in range(4):
+        sf, c64 = _inputs(sh, synth.SEED_BASE + 40 + i)
+        x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+        h = torch.empty(s["h"], dtype=torch.complex64, device="cuda")
+        R.rapro_receive_subframe(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"]), x, h_out=h)
+        o = oracle_receive(sh, c64, 12)
+        H = np.transpose(sf["H"], (1, 0, 2))[None]
+        err_h += np.sum(np.abs(_host(h) - H) ** 2)
+        err_h_o += np.sum(np.abs(o["h"] - H) ** 2)
+        pow_h += 2 * np.sum(np.abs(H) ** 2)
+        mu = 1.0 - o["s"]                                     # the oracle's unbiasing for both
+        T, D = sh.n_slots, sh.n_data_per_slot
+        xh = _host(x) / np.repeat(mu, D, axis=0)
+        err_x += np.sum(np.abs(xh - sf["x"]) ** 2)
+        err_x_o += np.sum(np.abs(o["xhat"] - sf["x"]) ** 2)
+        pow_x += np.sum(np.abs(sf["x"]) ** 2)
+    db = lambda v: 10 * np.log10(v)
+    assert abs(db(err_h / pow_h) - db(err_h_o / pow_h)) <= 0.1
+    assert abs(db(err_x / pow_x) - db(err_x_o / pow_x)) <= 0.1
