@@ -514,6 +514,60 @@ def run_rapro(args):
                                "estimator_hbm_frac": alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)}
             assert plb.device_status() == 0
 
+    # differentiable receive: forward + adjoint per subframe, and an Adam fit of (sigma2, tau)
+    diff = {}
+    if not args.no_sweep and rank == 0 and world == 1:
+        from paper_1802_05427_gb300 import autograd as AG
+        shd = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "K": 16, "snr_db": 15.0, "tau_rms": 6.0})
+        batch = []
+        for i in range(8):
+            sf = synth.make_subframe(shd, seed=synth.SEED_BASE + 3000 + i)
+            batch.append({k: torch.from_numpy(synth.as_c64(sf[k])).to(dev) for k in ("y_pilot", "pilots", "y_data")})
+            batch[-1]["x_ref"] = torch.from_numpy(synth.as_c64(sf["x"])).to(dev)
+        dshape = dict(M=shd.M, K=shd.K, n_sc=shd.n_sc, n_fft=shd.n_fft, subblock=12, qam_bits=shd.qam_bits,
+                      n_taps=shd.n_taps)
+        pd = R.make_params(**dshape, sigma2=shd.sigma2, tau_rms=shd.tau_rms)
+        with R.Plan(pd) as pld:
+            sd = pld.shapes()
+            hd = torch.empty(sd["h"], dtype=torch.complex64, device=dev)
+            ghd = torch.empty_like(hd)
+            xd = torch.empty(sd["x_eq"], dtype=torch.complex64, device=dev)
+            scd = torch.empty(2, dtype=torch.float32, device=dev)
+            gw = torch.empty((12, 12), dtype=torch.complex64, device=dev)
+
+            def fb(i):
+                d = batch[i % len(batch)]
+                R.rapro_receive_subframe(pld, d["y_pilot"], d["pilots"], d["y_data"], xd, h_out=hd)
+                R.rapro_mse_backward(pld, d["y_pilot"], d["pilots"], d["y_data"], hd, xd, d["x_ref"], ghd, scd, gw)
+            for i in range(3):
+                fb(i)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for i in range(32):
+                fb(i)
+            e1.record()
+            torch.cuda.synchronize()
+            diff["fwd_bwd_us_per_subframe"] = e0.elapsed_time(e1) * 1e3 / 32
+        theta0 = torch.tensor([2 * shd.sigma2, 2 * shd.tau_rms], dtype=torch.float64)
+        log_t = torch.log(theta0).clone().requires_grad_(True)
+        opt = torch.optim.Adam([log_t], lr=0.05)
+        t_fit = time.time()
+        l0 = None
+        for it in range(200):
+            opt.zero_grad()
+            l = AG.symbol_mse(torch.exp(log_t), batch, dshape)
+            l0 = float(l) if l0 is None else l0
+            l.backward()
+            opt.step()
+        fit = torch.exp(log_t.detach())
+        diff.update({"workload": f"{shd.M}x{shd.K}, {shd.n_sc} sc, 8 subframes, 16-QAM, 15 dB, tau 6, B = 12",
+                     "adam_steps": 200, "fit_seconds": time.time() - t_fit,
+                     "theta_true": [shd.sigma2, shd.tau_rms], "theta_init": theta0.tolist(), "theta_fit": fit.tolist(),
+                     "loss_init": l0, "loss_fit": float(AG.symbol_mse(fit, batch, dshape)),
+                     "loss_true": float(AG.symbol_mse(torch.tensor([shd.sigma2, shd.tau_rms], dtype=torch.float64),
+                                                      batch, dshape))})
+
     # comb pilots (Sec. II, IV-B) on the same 128 x 12 x 1200 shape: 12W, 3W, interpolated LS
     comb = {}
     if not args.no_sweep and rank == 0 and world == 1:
@@ -603,7 +657,7 @@ def run_rapro(args):
                     "api": "Receiver.receive_host (pinned host in/out, rapro_receive_subframe)"},
             "gpu_launches": 2 * args.steps, "clocks": clk,
             "kernels": rows, "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K,
-            "comb_pilots": comb, "precision_form": prec}
+            "comb_pilots": comb, "precision_form": prec, "differentiable": diff}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

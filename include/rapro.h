@@ -261,6 +261,38 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
                                     float* llr, int32_t* info, rapro_stream stream);
 
 /*
+ * Reverse mode of the symbol MSE, for fitting the model parameters of Eq. 13/17 (the paper
+ * fixes them by hand: L and SNR_fixed, Sec. IV-C) and sigma2 by gradient descent.  With the
+ * forward results h and x_eq of rapro_receive_subframe and known transmitted symbols
+ * x_ref [T*D][K][n_sc] (training data):
+ *   L = mean over (data symbol, user, subcarrier) of |x_eq - x_ref|^2.
+ * Outputs (device; gradients are conjugate Wirtinger gradients G = dL/dX*, i.e.
+ * dL = 2 Re sum conj(G) dX):
+ *   g_h       [T][K][M][n_sc]  dL/dh*  (detector adjoint of Eq. 22: sum_d y_d lambda_d^H -
+ *                              H sum_d (lambda_d x~_d^H + x~_d lambda_d^H), lambda_d = A^-1 g_d)
+ *   scalars   [2] floats       L, and dL/dsigma2 through the detector only (W held fixed)
+ *   g_w_main  [B][B]           dL/dW* of the shared block weights (sum over rows and blocks of
+ *                              g_h,blk h_ls,blk^H, Eq. 12), g_w_tail [tail][tail] likewise
+ * FP32 on the device, accumulated with atomics.  Orthogonal plans, B <= 64, n_sc <= 8192
+ * (RAPRO_ERR_UNSUPPORTED otherwise).  g_h must not alias an input.
+ */
+rapro_status rapro_mse_backward(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
+                                const rapro_c32* y_data, const rapro_c32* h, const rapro_c32* x_eq,
+                                const rapro_c32* x_ref, rapro_c32* g_h, float* scalars, rapro_c32* g_w_main,
+                                rapro_c32* g_w_tail, rapro_stream stream);
+
+/*
+ * Host-only FP64 chain rule through W = R (R + sigma2 I)^-1 (exponential PDP model):
+ * dW/dsigma2 = -W A^-1 and dW/dtau = (I - W) dR/dtau A^-1 with A = R + sigma2 I.
+ * g_w_main / g_w_tail: the weight gradients of rapro_mse_backward as interleaved doubles
+ * (g_w_tail may be NULL when B divides n_sc).  grad_out[0] = dL/dsigma2 and
+ * grad_out[1] = dL/dtau_rms through the estimator; the total dL/dsigma2 adds the
+ * detector's term from rapro_mse_backward.
+ */
+rapro_status rapro_weight_grad_host(const rapro_params* p, const double* g_w_main, const double* g_w_tail,
+                                    double* grad_out);
+
+/*
  * Allocation-free variant of rapro_receive_subframe (the paper has no counterpart; it
  * runs its receiver on host memory it allocates freely).  For callers that cannot
  * allocate device memory when a subframe arrives: code running inside a CUDA graph

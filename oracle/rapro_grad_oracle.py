@@ -105,9 +105,8 @@ def weight_grads(y_pilot, pilots, y_data, x, *, B, n_taps, n_fft, n_data_per_slo
                          n_data_per_slot=n_data_per_slot, sigma2_est=s_e, tau=ta, sigma2_det=s_d,
                          weights=(Wm, Wt))
     loss.backward()
-    # torch's gradient of a real loss w.r.t. a complex leaf is conj(dL/dz*) * 2 ... normalise
-    # to G = dL/dW* with dL = 2 Re sum conj(G) dW:  torch returns 2 * dL/dW* (the conjugate
-    # of the gradient convention), i.e. grad = 2 G.
+    # torch's .grad of a real loss with respect to a complex leaf is 2 dL/dW* (for L = |z|^2
+    # it is 2 z), so G = grad / 2.
     g_m = Wm.grad.numpy() / 2.0
     g_t = Wt.grad.numpy() / 2.0 if tail else None
     return float(loss.detach()), g_m, g_t, float(s_d.grad)

@@ -148,4 +148,27 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
                   "detection kernel launch");
 }
 
+rapro_status rapro_mse_backward(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
+                                const rapro_c32* y_data, const rapro_c32* h, const rapro_c32* x_eq,
+                                const rapro_c32* x_ref, rapro_c32* g_h, float* scalars, rapro_c32* g_w_main,
+                                rapro_c32* g_w_tail, rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  if (!y_pilot || !pilots || !y_data || !h || !x_eq || !x_ref || !g_h || !scalars || !g_w_main ||
+      (pl->tail && !g_w_tail))
+    return bad("every array except g_w_tail (when B divides n_sc) is required");
+  const void* g = g_h;
+  if (g == y_pilot || g == y_data || g == h || g == x_eq || g == x_ref) return bad("g_h must not alias an input");
+  rapro_status s = check_device(pl);
+  if (s == RAPRO_OK) s = orthogonal_only(pl);
+  if (s != RAPRO_OK) return s;
+  if (pl->B > adjoint_max_block() || pl->p.n_sc > 8192) {
+    set_error("the adjoint supports subblock <= 64 and n_sc <= 8192");
+    return RAPRO_ERR_UNSUPPORTED;
+  }
+  return launched(launch_adjoint(*pl, f2(y_pilot), f2(pilots), f2(y_data), f2(h), f2(x_eq), f2(x_ref), f2(g_h),
+                                 scalars, f2(g_w_main), f2(g_w_tail), cs(stream)),
+                  "adjoint launch");
+}
+
 }  // extern "C"

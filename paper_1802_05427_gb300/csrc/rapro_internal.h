@@ -71,6 +71,13 @@ bool build_comb_weights_fp64(const rapro_params& p, std::vector<double>& w_out);
 cudaError_t launch_comb(const Plan& pl, const float2* y, const float2* pil, float2* h, cudaStream_t st);
 cudaError_t prepare_comb(int device);
 
+// Reverse mode of the symbol MSE (k_adjoint.cu); weights' chain rule on the host.
+int adjoint_max_block();
+cudaError_t launch_adjoint(const Plan& pl, const float2* y_pilot, const float2* pilots, const float2* y_data,
+                           const float2* h, const float2* x_eq, const float2* x_ref, float2* g_h, float* scal,
+                           float2* g_wm, float2* g_wt, cudaStream_t st);
+cudaError_t prepare_adjoint(int device);
+
 // Kernel launchers (return the launch error, if any).
 cudaError_t launch_ls(const float2* y, const float2* pil, float2* h, int T, int K, int M,
                       int N, cudaStream_t st);

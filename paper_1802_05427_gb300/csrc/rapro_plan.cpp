@@ -286,6 +286,97 @@ rapro_status rapro_build_weights_host(const rapro_params* p, int block_len, doub
   return RAPRO_OK;
 }
 
+rapro_status rapro_weight_grad_host(const rapro_params* p, const double* g_w_main, const double* g_w_tail,
+                                    double* grad_out) {
+  rapro_status s = rapro_params_validate(p);
+  if (s != RAPRO_OK) return s;
+  if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL || p->pdp != RAPRO_PDP_EXP) {
+    set_error("the weight gradient covers the sub-block weights of the exponential PDP model");
+    return RAPRO_ERR_UNSUPPORTED;
+  }
+  const int B = p->subblock, tail = p->n_sc % B;
+  if (!g_w_main || !grad_out || (tail && !g_w_tail)) return invalid("g_w_main, grad_out (and g_w_tail) are required");
+  if (B > 512) return invalid("block size above 512");
+  // dp_l/dtau = p_l (l - lbar) / tau^2 for p_l = exp(-l/tau) / sum; r'(d) = sum_l dp_l e^{-j 2 pi l d / n_fft}.
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> pl(p->n_taps);
+  double norm = 0.0, lbar = 0.0;
+  for (int l = 0; l < p->n_taps; ++l) norm += (pl[l] = std::exp(-l / p->tau_rms));
+  for (int l = 0; l < p->n_taps; ++l) lbar += (pl[l] /= norm) * l;
+  auto dcorr = [&](int d) {
+    cd acc(0.0, 0.0);
+    for (int l = 0; l < p->n_taps; ++l) {
+      const double ph = -two_pi * double(l) * double(d) / double(p->n_fft);
+      acc += (pl[l] * (l - lbar) / (p->tau_rms * p->tau_rms)) * cd(std::cos(ph), std::sin(ph));
+    }
+    return acc;
+  };
+  double g_s2 = 0.0, g_tau = 0.0;
+  for (int part = 0; part < (tail ? 2 : 1); ++part) {
+    const int n = part ? tail : B;
+    const double* G = part ? g_w_tail : g_w_main;
+    // A = R + sigma2 I = L L^H; Ainv by solves on the identity; W = R Ainv.
+    std::vector<cd> R(size_t(n) * n), dR(size_t(n) * n), L(size_t(n) * n), Ai(size_t(n) * n), y(n);
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        R[size_t(a) * n + b] = corr(*p, a - b);
+        dR[size_t(a) * n + b] = dcorr(a - b);
+      }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j <= i; ++j) L[size_t(i) * n + j] = R[size_t(i) * n + j] + (i == j ? p->sigma2 : 0.0);
+    for (int j = 0; j < n; ++j) {
+      cd* Lj = &L[size_t(j) * n];
+      double d = Lj[j].real();
+      for (int k = 0; k < j; ++k) d -= std::norm(Lj[k]);
+      if (!(d > 0.0) || !std::isfinite(d)) {
+        set_error("R + sigma2 I is not positive definite in FP64");
+        return RAPRO_ERR_NOT_POSDEF;
+      }
+      const double ljj = std::sqrt(d);
+      Lj[j] = cd(ljj, 0.0);
+      for (int i = j + 1; i < n; ++i) {
+        cd* Li = &L[size_t(i) * n];
+        cd sum = Li[j];
+        for (int k = 0; k < j; ++k) sum -= Li[k] * std::conj(Lj[k]);
+        Li[j] = sum / ljj;
+      }
+    }
+    for (int c = 0; c < n; ++c) {
+      for (int i = 0; i < n; ++i) {
+        cd sum = (i == c) ? cd(1.0, 0.0) : cd(0.0, 0.0);
+        for (int k = 0; k < i; ++k) sum -= L[size_t(i) * n + k] * y[k];
+        y[i] = sum / L[size_t(i) * n + i].real();
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        cd sum = y[i];
+        for (int k = i + 1; k < n; ++k) sum -= std::conj(L[size_t(k) * n + i]) * Ai[size_t(k) * n + c];
+        Ai[size_t(i) * n + c] = sum / L[size_t(i) * n + i].real();
+      }
+    }
+    auto mul = [n](const std::vector<cd>& X, const std::vector<cd>& Y) {
+      std::vector<cd> Z(size_t(n) * n, cd(0.0, 0.0));
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j) Z[size_t(i) * n + j] += X[size_t(i) * n + k] * Y[size_t(k) * n + j];
+      return Z;
+    };
+    const std::vector<cd> W = mul(R, Ai);
+    const std::vector<cd> dWs = mul(W, Ai);                 // dW/dsigma2 = -W Ainv
+    std::vector<cd> ImW(size_t(n) * n);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) ImW[size_t(i) * n + j] = (i == j ? 1.0 : 0.0) - W[size_t(i) * n + j];
+    const std::vector<cd> dWt = mul(mul(ImW, dR), Ai);      // dW/dtau = (I - W) dR Ainv
+    for (size_t e = 0; e < size_t(n) * n; ++e) {
+      const cd g(G[2 * e], G[2 * e + 1]);
+      g_s2 += 2.0 * (std::conj(g) * (-dWs[e])).real();
+      g_tau += 2.0 * (std::conj(g) * dWt[e]).real();
+    }
+  }
+  grad_out[0] = g_s2;
+  grad_out[1] = g_tau;
+  return RAPRO_OK;
+}
+
 rapro_status rapro_build_comb_weights_host(const rapro_params* p, double* w_out) {
   rapro_status s = rapro_params_validate(p);
   if (s != RAPRO_OK) return s;
@@ -355,6 +446,7 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if ((e = prepare_estimate(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "estimator set-up"); }
   if ((e = prepare_lmmse_tc(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core estimator set-up"); }
   if ((e = prepare_comb(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "comb estimator set-up"); }
+  if ((e = prepare_adjoint(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "adjoint set-up"); }
   const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);

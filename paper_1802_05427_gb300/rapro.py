@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
         "rapro_build_weights_host": ([ctypes.POINTER(RaproParams), ctypes.c_int, _P], ctypes.c_int),
         "rapro_build_comb_weights_host": ([ctypes.POINTER(RaproParams), _P], ctypes.c_int),
         "rapro_ce_comb": ([_P, _P, _P, _P, _P], ctypes.c_int),
+        "rapro_mse_backward": ([_P] * 12, ctypes.c_int),
+        "rapro_weight_grad_host": ([ctypes.POINTER(RaproParams), _P, _P, _P], ctypes.c_int),
         "rapro_plan_create": ([ctypes.POINTER(RaproParams), ctypes.POINTER(_P)], ctypes.c_int),
         "rapro_plan_destroy": ([_P], ctypes.c_int),
         "rapro_plan_dims": ([_P, _P, _P, _P, _P], ctypes.c_int),
@@ -251,6 +253,33 @@ def rapro_ce_comb(plan: Plan, y_pilot, pilots, h, stream=None) -> None:
     _check(lib().rapro_ce_comb(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
                                _ptr(pilots, s["pilots"], c64, "pilots"), _ptr(h, s["h"], c64, "h"),
                                _stream(stream)), "rapro_ce_comb")
+
+
+def rapro_mse_backward(plan: Plan, y_pilot, pilots, y_data, h, x_eq, x_ref, g_h, scalars, g_w_main,
+                       g_w_tail=None, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    B, tail = plan.params.subblock, plan.tail
+    _check(lib().rapro_mse_backward(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
+                                    _ptr(pilots, s["pilots"], c64, "pilots"), _ptr(y_data, s["y_data"], c64, "y_data"),
+                                    _ptr(h, s["h"], c64, "h"), _ptr(x_eq, s["x_eq"], c64, "x_eq"),
+                                    _ptr(x_ref, s["x_eq"], c64, "x_ref"), _ptr(g_h, s["h"], c64, "g_h"),
+                                    _ptr(scalars, (2,), torch.float32, "scalars"),
+                                    _ptr(g_w_main, (B, B), c64, "g_w_main"),
+                                    _ptr(g_w_tail, (tail, tail), c64, "g_w_tail") if tail else None,
+                                    _stream(stream)), "rapro_mse_backward")
+
+
+def rapro_weight_grad_host(p: RaproParams, g_w_main, g_w_tail=None):
+    """(dL/dsigma2, dL/dtau_rms) through the estimator weights, FP64 on the host."""
+    import numpy as np
+    gm = np.ascontiguousarray(np.asarray(g_w_main, dtype=np.complex128)).view(np.float64)
+    gt = None if g_w_tail is None else np.ascontiguousarray(np.asarray(g_w_tail, dtype=np.complex128)).view(np.float64)
+    out = np.zeros(2, dtype=np.float64)
+    _check(lib().rapro_weight_grad_host(ctypes.byref(p), gm.ctypes.data, None if gt is None else gt.ctypes.data,
+                                        out.ctypes.data), "rapro_weight_grad_host")
+    return float(out[0]), float(out[1])
 
 
 def rapro_mmse_detect(plan: Plan, h, y_data, x_eq, labels=None, llr=None, info=None, stream=None) -> None:

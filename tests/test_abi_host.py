@@ -145,3 +145,27 @@ def test_precision_validation(lib):
         assert R.rapro_params_validate(p) == R.RAPRO_ERR_UNSUPPORTED
     p.subblock, p.precision = 12, 5
     assert R.rapro_params_validate(p) == R.RAPRO_ERR_INVALID_ARG
+
+
+# --------------------------------------------------------- weight gradient (host)
+@pytest.mark.parametrize("B", [1, 5, 12, 30])
+def test_host_weight_gradient_matches_autograd(lib, B):
+    """rapro_weight_grad_host: 2 Re sum conj(G) dW/dtheta equals torch.autograd of the same
+    contraction through the differentiable oracle's W(sigma2, tau)."""
+    import torch
+    from oracle import rapro_grad_oracle as G
+    sh = synth.SubframeShape(M=4, K=2, n_sc=62, n_fft=128, n_taps=7, tau_rms=2.5, snr_db=9.0)
+    p = params_for(sh, B)
+    rng = np.random.default_rng(B)
+    tail = sh.n_sc % B
+    gm = rng.standard_normal((B, B)) + 1j * rng.standard_normal((B, B))
+    gt = rng.standard_normal((tail, tail)) + 1j * rng.standard_normal((tail, tail)) if tail else None
+    d_s2, d_tau = R.rapro_weight_grad_host(p, gm, gt)
+    s2 = torch.tensor(sh.sigma2, dtype=torch.float64, requires_grad=True)
+    tau = torch.tensor(sh.tau_rms, dtype=torch.float64, requires_grad=True)
+    f = 2 * torch.real(torch.sum(torch.conj(torch.as_tensor(gm)) * G.block_weight(B, s2, tau, sh.n_taps, sh.n_fft)))
+    if tail:
+        f = f + 2 * torch.real(torch.sum(torch.conj(torch.as_tensor(gt)) *
+                                         G.block_weight(tail, s2, tau, sh.n_taps, sh.n_fft)))
+    f.backward()
+    np.testing.assert_allclose([d_s2, d_tau], [float(s2.grad), float(tau.grad)], rtol=1e-9, atol=1e-12)

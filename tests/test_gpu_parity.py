@@ -17,6 +17,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import rapro_oracle as O
+from oracle import rapro_grad_oracle as G
 from paper_1802_05427_gb300 import _build, synth
 from paper_1802_05427_gb300 import rapro as R
 
@@ -445,3 +446,97 @@ def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db():
     db = lambda v: 10 * np.log10(v)
     assert abs(db(err_h / pow_h) - db(err_h_o / pow_h)) <= 0.1
     assert abs(db(err_x / pow_x) - db(err_x_o / pow_x)) <= 0.1
+
+
+# ------------------------------------------------- differentiable receive (adjoint)
+ADJ_CASES = [
+    # M, K, N, n_fft, B, D
+    (6, 2, 30, 64, 7, 3), (32, 4, 120, 256, 12, 6), (17, 5, 100, 256, 9, 4), (128, 16, 1200, 2048, 12, 6),
+]
+
+
+def _adj_inputs(M, K, N, nfft, B, D, seed):
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=5 if nfft < 2048 else 24,
+                             tau_rms=3.0 if nfft < 2048 else 6.0, snr_db=12.0, qam_bits=4, n_data_per_slot=D)
+    sf = synth.make_subframe(sh, seed=seed)
+    c64 = {k: synth.as_c64(sf[k]) for k in ("y_pilot", "pilots", "y_data", "x")}
+    return sh, sf, c64
+
+
+@pytest.mark.parametrize("case", ADJ_CASES)
+def test_mse_backward_matches_the_differentiable_oracle(case):
+    """Loss, dL/dW* (main and tail), the detector's dL/dsigma2 and the total gradient in
+    (sigma2, tau) against torch.autograd of the FP64 oracle (FP32 adjoint: 1e-3 relative)."""
+    M, K, N, nfft, B, D = case
+    sh, sf, c64 = _adj_inputs(M, K, N, nfft, B, D, seed=synth.SEED_BASE + 50)
+    s2, tau = 1.7 * sh.sigma2, 0.8 * sh.tau_rms          # off the generator's values
+    p = params_for(sh, B)
+    p.sigma2, p.tau_rms = s2, tau
+    plan = R.Plan(p)
+    s = plan.shapes()
+    tail = plan.tail
+    h = torch.empty(s["h"], dtype=torch.complex64, device="cuda")
+    g_h = torch.empty_like(h)
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+    scal = torch.empty(2, dtype=torch.float32, device="cuda")
+    gwm = torch.empty((B, B), dtype=torch.complex64, device="cuda")
+    gwt = torch.empty((tail, tail), dtype=torch.complex64, device="cuda") if tail else None
+    yp, pil, yd, xr = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"]), _dev(c64["x"])
+    R.rapro_receive_subframe(plan, yp, pil, yd, x, h_out=h)
+    R.rapro_mse_backward(plan, yp, pil, yd, h, x, xr, g_h, scal, gwm, gwt)
+    sc = _host(scal).astype(np.float64)
+    kw = dict(B=B, n_taps=sh.n_taps, n_fft=sh.n_fft, n_data_per_slot=D, sigma2_est=s2, tau=tau, sigma2_det=s2)
+    ins = [c64[k].astype(np.complex128) for k in ("y_pilot", "pilots", "y_data", "x")]
+    loss_o, g_m, g_t, g_sd = G.weight_grads(*ins, **kw)
+    assert abs(sc[0] - loss_o) <= 1e-5 * loss_o
+    assert abs(sc[1] - g_sd) <= 1e-3 * abs(g_sd)
+    assert np.linalg.norm(_host(gwm) - g_m) <= 1e-3 * np.linalg.norm(g_m)
+    if tail:
+        assert np.linalg.norm(_host(gwt) - g_t) <= 1e-3 * np.linalg.norm(g_t)
+    _, g_se, g_tau, g_sd2 = G.grads(*ins, **kw)
+    d_s2_w, d_tau = R.rapro_weight_grad_host(p, _host(gwm).astype(np.complex128),
+                                             _host(gwt).astype(np.complex128) if tail else None)
+    np.testing.assert_allclose([sc[1] + d_s2_w, d_tau], [g_se + g_sd2, g_tau], rtol=2e-3, atol=1e-9)
+
+
+def test_autograd_function_and_adam_fit_of_the_channel_statistics():
+    """torch.autograd.Function over the CUDA forward and adjoint: its gradient matches central
+    differences of the CUDA loss, and 200 Adam steps from (2 sigma2, 2 tau) lower the loss to
+    that at the true statistics and move (sigma2, tau) towards them."""
+    from paper_1802_05427_gb300 import autograd as AG
+    sh = synth.SubframeShape(M=64, K=8, n_sc=600, n_fft=1024, n_taps=16, tau_rms=6.0, snr_db=15.0,
+                             qam_bits=4)
+    B = 12
+    batch = []
+    for i in range(4):
+        sf = synth.make_subframe(sh, seed=synth.SEED_BASE + 60 + i)
+        batch.append({k: _dev(synth.as_c64(sf[k])) for k in ("y_pilot", "pilots", "y_data")})
+        batch[-1]["x_ref"] = _dev(synth.as_c64(sf["x"]))
+    shape = dict(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, qam_bits=sh.qam_bits, n_taps=sh.n_taps)
+    theta = torch.tensor([2 * sh.sigma2, 2 * sh.tau_rms], dtype=torch.float64, requires_grad=True)
+    loss = AG.symbol_mse(theta, batch, shape)
+    loss.backward()
+    for i, rel in ((0, 1e-2), (1, 1e-2)):
+        e = torch.zeros(2, dtype=torch.float64)
+        step = 1e-2 * float(theta.detach()[i])
+        e[i] = step
+        fd = (float(AG.symbol_mse(theta.detach() + e, batch, shape)) -
+              float(AG.symbol_mse(theta.detach() - e, batch, shape))) / (2 * step)
+        assert abs(float(theta.grad[i]) - fd) <= rel * abs(fd) + 1e-7, (i, float(theta.grad[i]), fd)
+    truth = torch.tensor([sh.sigma2, sh.tau_rms], dtype=torch.float64)
+    l_true = float(AG.symbol_mse(truth, batch, shape))
+    log_theta = torch.log(theta.detach()).clone().requires_grad_(True)
+    opt = torch.optim.Adam([log_theta], lr=0.05)
+    l0 = None
+    for it in range(200):
+        opt.zero_grad()
+        l = AG.symbol_mse(torch.exp(log_theta), batch, shape)
+        if l0 is None:
+            l0 = float(l)
+        l.backward()
+        opt.step()
+    fit = torch.exp(log_theta.detach())
+    l_fit = float(AG.symbol_mse(fit, batch, shape))
+    assert l_fit < l0 and l_fit <= 1.01 * l_true, (l0, l_fit, l_true)
+    for i in range(2):
+        assert abs(np.log(float(fit[i] / truth[i]))) < 0.5 * np.log(2.0), (fit, truth)
