@@ -557,7 +557,7 @@ def run_rapro(args):
         for it in range(200):
             opt.zero_grad()
             l = AG.symbol_mse(torch.exp(log_t), batch, dshape)
-            l0 = float(l) if l0 is None else l0
+            l0 = float(l.detach()) if l0 is None else l0
             l.backward()
             opt.step()
         fit = torch.exp(log_t.detach())

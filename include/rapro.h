@@ -273,7 +273,7 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
  *   scalars   [2] floats       L, and dL/dsigma2 through the detector only (W held fixed)
  *   g_w_main  [B][B]           dL/dW* of the shared block weights (sum over rows and blocks of
  *                              g_h,blk h_ls,blk^H, Eq. 12), g_w_tail [tail][tail] likewise
- * FP32 on the device, accumulated with atomics.  Orthogonal plans, B <= 64, n_sc <= 8192
+ * FP32 on the device, accumulated with atomics.  Orthogonal plans, B <= 64, n_sc <= 2048
  * (RAPRO_ERR_UNSUPPORTED otherwise).  g_h must not alias an input.
  */
 rapro_status rapro_mse_backward(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,

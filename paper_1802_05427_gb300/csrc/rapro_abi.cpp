@@ -162,8 +162,8 @@ rapro_status rapro_mse_backward(const rapro_plan* plan, const rapro_c32* y_pilot
   rapro_status s = check_device(pl);
   if (s == RAPRO_OK) s = orthogonal_only(pl);
   if (s != RAPRO_OK) return s;
-  if (pl->B > adjoint_max_block() || pl->p.n_sc > 8192) {
-    set_error("the adjoint supports subblock <= 64 and n_sc <= 8192");
+  if (pl->B > adjoint_max_block() || pl->p.n_sc > adjoint_max_subcarriers()) {
+    set_error("the adjoint supports subblock <= 64 and n_sc <= 2048");
     return RAPRO_ERR_UNSUPPORTED;
   }
   return launched(launch_adjoint(*pl, f2(y_pilot), f2(pilots), f2(y_data), f2(h), f2(x_eq), f2(x_ref), f2(g_h),

@@ -73,6 +73,7 @@ cudaError_t prepare_comb(int device);
 
 // Reverse mode of the symbol MSE (k_adjoint.cu); weights' chain rule on the host.
 int adjoint_max_block();
+int adjoint_max_subcarriers();
 cudaError_t launch_adjoint(const Plan& pl, const float2* y_pilot, const float2* pilots, const float2* y_data,
                            const float2* h, const float2* x_eq, const float2* x_ref, float2* g_h, float* scal,
                            float2* g_wm, float2* g_wt, cudaStream_t st);
