@@ -27,6 +27,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -109,6 +111,86 @@ def measured_traffic(kernel):
         return None
     v = t.get("kernels", {}).get(kernel)
     return None if v is None else float(v)
+
+
+# ------------------------------------------------- batched heterogeneous workload
+def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3):
+    """512 jobs: M ~ U{32,64,128,256}, K ~ U{4,8,12,16}, n_sc ~ U{72,300,600,1200} (FFT the next of
+    128/512/1024/2048), 2/4/6-bit QAM, SNR ~ U[0,25] dB, tau ~ U[2,12], B ~ U{12,48}; inputs are
+    seeded device Gaussians with unit-modulus pilots (the kernels' work does not depend on the
+    values).  One CUDA graph of rapro_receive_batch over all jobs, 8 streams vs 1 stream, and
+    after rapro_plan_tune on every plan."""
+    import torch
+    from paper_1802_05427_gb300 import rapro as R
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    fft_of = {72: 128, 300: 512, 600: 1024, 1200: 2048}
+    jobs, res = [], 0
+    for _ in range(n_jobs):
+        M = int(rng.choice([32, 64, 128, 256]))
+        K = int(rng.choice([4, 8, 12, 16]))
+        N = int(rng.choice([72, 300, 600, 1200]))
+        q = int(rng.choice([2, 4, 6]))
+        snr = float(rng.uniform(0.0, 25.0))
+        tau = float(rng.uniform(2.0, 12.0))
+        B = int(rng.choice([12, 48]))
+        p = R.make_params(M=M, K=K, n_sc=N, n_fft=fft_of[N], subblock=B, sigma2=10 ** (-snr / 10), qam_bits=q,
+                          n_taps=16, tau_rms=tau)
+        pl = R.Plan(p)
+        s = pl.shapes()
+
+        def cn(shape):
+            return torch.complex(torch.randn(shape, generator=gen, device=dev),
+                                 torch.randn(shape, generator=gen, device=dev)).contiguous()
+        th = torch.rand(s["pilots"], generator=gen, device=dev) * (2 * np.pi)
+        jobs.append(dict(plan=pl, y_pilot=cn(s["y_pilot"]), pilots=torch.polar(torch.ones_like(th), th).contiguous(),
+                         y_data=cn(s["y_data"]), x_eq=torch.empty(s["x_eq"], dtype=torch.complex64, device=dev),
+                         labels=torch.empty(s["labels"], dtype=torch.uint8, device=dev)))
+        res += pl.T * pl.D * N
+    torch.cuda.synchronize()
+
+    def timed(n_streams, reps=5):
+        batch = R.Batch(n_streams)
+        R.rapro_receive_batch(batch, jobs)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                R.rapro_receive_batch(batch, jobs, stream=st)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        batch.close()
+        return e0.elapsed_time(e1) / reps
+
+    ms8, ms1 = timed(8), timed(1)
+    t0 = time.time()
+    for j in jobs:
+        s = j["plan"].shapes()
+        h = torch.empty(s["h"], dtype=torch.complex64, device=dev)
+        R.rapro_plan_tune(j["plan"], j["y_pilot"], j["pilots"], j["y_data"], h, j["x_eq"])
+    tune_s = time.time() - t0
+    ms8t = timed(8)
+    counts = {}
+    for j in jobs:
+        ev, _ = R.rapro_plan_variant(j["plan"])
+        counts[str(ev)] = counts.get(str(ev), 0) + 1
+    for j in jobs:
+        assert j["plan"].device_status() == 0
+        j["plan"].close()
+    return {"jobs": n_jobs, "res_per_batch": res, "ms_per_batch_8_streams": ms8, "ms_per_batch_1_stream": ms1,
+            "res_per_s_8_streams": res / (ms8 * 1e-3), "res_per_s_1_stream": res / (ms1 * 1e-3),
+            "res_per_s_8_streams_tuned": res / (ms8t * 1e-3), "tune_seconds": tune_s,
+            "tuned_estimator_kernels": counts,
+            "inputs": "seeded device Gaussians (unit-modulus pilots), one CUDA graph per batch"}
 
 
 # ------------------------------------------------------------ multi-rank
@@ -568,6 +650,11 @@ def run_rapro(args):
                      "loss_true": float(AG.symbol_mse(torch.tensor([shd.sigma2, shd.tau_rms], dtype=torch.float64),
                                                       batch, dshape))})
 
+    # batched heterogeneous receive: 512 subframes of uneven shapes in one call / one graph
+    hetero = {}
+    if not args.no_sweep and rank == 0 and world == 1:
+        hetero = hetero_batch(dev)
+
     # comb pilots (Sec. II, IV-B) on the same 128 x 12 x 1200 shape: 12W, 3W, interpolated LS
     comb = {}
     if not args.no_sweep and rank == 0 and world == 1:
@@ -657,7 +744,8 @@ def run_rapro(args):
                     "api": "Receiver.receive_host (pinned host in/out, rapro_receive_subframe)"},
             "gpu_launches": 2 * args.steps, "clocks": clk,
             "kernels": rows, "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K,
-            "comb_pilots": comb, "precision_form": prec, "differentiable": diff}
+            "comb_pilots": comb, "precision_form": prec, "differentiable": diff,
+            "batched_heterogeneous": hetero}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

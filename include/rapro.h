@@ -261,6 +261,49 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
                                     float* llr, int32_t* info, rapro_stream stream);
 
 /*
+ * Autotuner (no counterpart in the paper, whose receiver has one code path): times every
+ * estimator kernel that applies to the plan's shape and these arrays (tensor cores,
+ * streaming, row-segment and tiled kernels; comb plans have one) and the detector's
+ * warps-per-role split, 2 warm and 5 timed launches each on the caller's stream, and keeps
+ * the fastest in the plan (later calls with arrays the choice does not apply to fall back
+ * to the built-in choice).  Overwrites h and x_eq.  Synchronises the stream; not inside a
+ * stream capture.  The plan must not be in use by another stream meanwhile.
+ */
+rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
+                             const rapro_c32* y_data, rapro_c32* h, rapro_c32* x_eq, rapro_stream stream);
+
+/* The plan's kernel choices: estimator kernel (-1 built-in, 0 tensor cores, 1 streaming,
+ * 2 row segments, 3 tiled) and the detector's warps per role.  Either pointer may be NULL. */
+rapro_status rapro_plan_variant(const rapro_plan* plan, int* est_variant, int* det_split);
+
+/*
+ * Batched heterogeneous receive: many independent subframes, each with its own plan (any
+ * shapes, layouts and precisions), in one call.  The library's pool of n_streams CUDA
+ * streams (rapro_batch_create, 1..32) runs them side by side: the jobs go longest first
+ * (estimated multiply-accumulates) onto the least loaded stream, forked from and joined back
+ * into the caller's stream with events, so the call can be captured into one CUDA graph and
+ * returns "enqueued" like the single-subframe call.  Jobs that share a plan must pass h_out
+ * (the plan's workspace holds one estimate).  Arguments of each job as for
+ * rapro_receive_subframe; one bad job returns its status after the jobs before it were
+ * enqueued and the streams joined.
+ */
+typedef struct rapro_batch rapro_batch;
+typedef struct {
+  const rapro_plan* plan;
+  const rapro_c32* y_pilot;
+  const rapro_c32* pilots;
+  const rapro_c32* y_data;
+  rapro_c32* h_out;      /* nullable: the plan's workspace */
+  rapro_c32* x_eq;
+  uint8_t* labels;       /* nullable */
+  float* llr;            /* nullable */
+  int32_t* info;         /* nullable */
+} rapro_job;
+rapro_status rapro_batch_create(int n_streams, rapro_batch** out);
+rapro_status rapro_batch_destroy(rapro_batch* batch);   /* synchronises the device; NULL is a no-op */
+rapro_status rapro_receive_batch(rapro_batch* batch, const rapro_job* jobs, int n_jobs, rapro_stream stream);
+
+/*
  * Reverse mode of the symbol MSE, for fitting the model parameters of Eq. 13/17 (the paper
  * fixes them by hand: L and SNR_fixed, Sec. IV-C) and sigma2 by gradient descent.  With the
  * forward results h and x_eq of rapro_receive_subframe and known transmitted symbols

@@ -267,10 +267,10 @@ static cudaError_t launch_stream(const WSmall<BM>& W0, const float2* y, const fl
 
 template <int BM>
 static cudaError_t launch_small(const Plan& pl, const float2* x, const float2* pil, float2* out,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool allow_stream = true) {
   WSmall<BM> W;
   fill_small<BM>(W, pl.w_main.data(), pl.w_tail.data(), pl.B, pl.tail);
-  if (pil && stream_ok(x, pil, out, pl.p.n_sc, pl.B, pl.nb))
+  if (allow_stream && pil && stream_ok(x, pil, out, pl.p.n_sc, pl.B, pl.nb))
     return launch_stream<BM>(W, x, pil, out, pl.T, pl.p.K, pl.p.M, pl.p.n_sc, pl.B, pl.nb, pl.tail,
                              pl.d_status, st);
   const int rows = pl.T * pl.p.K * pl.p.M;
@@ -430,16 +430,39 @@ cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
   // d_w_main != plan weights means a caller override with one W per block.
   const bool override_w = d_w_main != pl.d_w_main;
   if (override_w) return launch_tiled(pl, x, pil, d_w_main, nullptr, 1, out, st);
-  if (lmmse_tc_ok(pl, x, pil, out)) return launch_lmmse_tc(pl, x, pil, out, st);
-  if (pl.p.precision == RAPRO_PREC_BF16) return cudaErrorNotSupported;   // never a silent FP32 fallback
+  return launch_lmmse_variant(pl, pl.est_variant, x, pil, out, st);
+}
+
+bool lmmse_variant_ok(const Plan& pl, int v, const float2* x, const float2* pil, const float2* out) {
+  if (pl.p.precision == RAPRO_PREC_BF16) return v == EST_TC && lmmse_tc_ok(pl, x, pil, out);
+  switch (v) {
+    case EST_TC: return lmmse_tc_ok(pl, x, pil, out);
+    case EST_STREAM: return pil && pl.B <= LMMSE_SMALL_MAX && stream_ok(x, pil, out, pl.p.n_sc, pl.B, pl.nb);
+    case EST_SMALL: return pl.B <= LMMSE_SMALL_MAX;
+    case EST_TILED: return true;
+    default: return false;
+  }
+}
+
+// Variant v (EST_*), or the built-in choice for v < 0 or a variant that does not apply to
+// these arrays: tensor cores, then the streaming / segment kernels, then the tiled one.
+cudaError_t launch_lmmse_variant(const Plan& pl, int v, const float2* x, const float2* pil, float2* out,
+                                 cudaStream_t st) {
+  if (v < 0 || !lmmse_variant_ok(pl, v, x, pil, out)) {
+    if (lmmse_tc_ok(pl, x, pil, out)) return launch_lmmse_tc(pl, x, pil, out, st);
+    if (pl.p.precision == RAPRO_PREC_BF16) return cudaErrorNotSupported;   // never a silent FP32 fallback
+    v = pl.B <= LMMSE_SMALL_MAX ? EST_STREAM : EST_TILED;
+  }
+  if (v == EST_TC) return launch_lmmse_tc(pl, x, pil, out, st);
+  if (v == EST_TILED) return launch_tiled(pl, x, pil, pl.d_w_main, pl.d_w_tail, 0, out, st);
+  const bool stream = v == EST_STREAM;
   const int B = pl.B;
-  if (B <= 4) return launch_small<4>(pl, x, pil, out, st);
-  if (B <= 8) return launch_small<8>(pl, x, pil, out, st);
-  if (B <= 12) return launch_small<12>(pl, x, pil, out, st);
-  if (B <= 16) return launch_small<16>(pl, x, pil, out, st);
-  if (B <= 24) return launch_small<24>(pl, x, pil, out, st);
-  if (B <= LMMSE_SMALL_MAX) return launch_small<32>(pl, x, pil, out, st);
-  return launch_tiled(pl, x, pil, d_w_main, d_w_tail, 0, out, st);
+  if (B <= 4) return launch_small<4>(pl, x, pil, out, st, stream);
+  if (B <= 8) return launch_small<8>(pl, x, pil, out, st, stream);
+  if (B <= 12) return launch_small<12>(pl, x, pil, out, st, stream);
+  if (B <= 16) return launch_small<16>(pl, x, pil, out, st, stream);
+  if (B <= 24) return launch_small<24>(pl, x, pil, out, st, stream);
+  return launch_small<32>(pl, x, pil, out, st, stream);
 }
 
 }  // namespace rapro

@@ -56,6 +56,27 @@ inline cudaStream_t cs(rapro_stream s) { return reinterpret_cast<cudaStream_t>(s
 
 }  // namespace
 
+namespace rapro {
+
+// One subframe through the estimator and the detector on stream st (rapro_receive_subframe).
+rapro_status receive_on(const Plan* pl, const rapro_c32* y_pilot, const rapro_c32* pilots, const rapro_c32* y_data,
+                        rapro_c32* h_out, rapro_c32* x_eq, uint8_t* labels, float* llr, int32_t* info,
+                        cudaStream_t st) {
+  if (!y_pilot || !pilots || !y_data || !x_eq)
+    return bad("y_pilot, pilots, y_data and x_eq must not be NULL");
+  rapro_status s = check_device(pl);
+  if (s != RAPRO_OK) return s;
+  float2* h = h_out ? f2(h_out) : pl->d_h_work;
+  if ((s = bf16_check(pl, y_pilot, pilots, h, nullptr)) != RAPRO_OK) return s;
+  cudaError_t e = pl->comb ? launch_comb(*pl, f2(y_pilot), f2(pilots), h, st)
+                           : launch_lmmse(*pl, f2(y_pilot), f2(pilots), pl->d_w_main, pl->d_w_tail,
+                                          pl->w_main.data(), pl->w_tail.data(), h, st);
+  if (e != cudaSuccess) return cuda_fail(e, "channel estimator launch");
+  return launched(launch_detect(*pl, h, f2(y_data), f2(x_eq), labels, llr, info, st), "detection kernel launch");
+}
+
+}  // namespace rapro
+
 extern "C" {
 
 rapro_status rapro_ce_ls(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
@@ -133,19 +154,8 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
                                     rapro_c32* h_out, rapro_c32* x_eq, uint8_t* labels, float* llr,
                                     int32_t* info, rapro_stream stream) {
   if (!plan) return bad("plan is NULL");
-  if (!y_pilot || !pilots || !y_data || !x_eq)
-    return bad("y_pilot, pilots, y_data and x_eq must not be NULL");
-  const Plan* pl = reinterpret_cast<const Plan*>(plan);
-  rapro_status s = check_device(pl);
-  if (s != RAPRO_OK) return s;
-  float2* h = h_out ? f2(h_out) : pl->d_h_work;
-  if ((s = bf16_check(pl, y_pilot, pilots, h, nullptr)) != RAPRO_OK) return s;
-  cudaError_t e = pl->comb ? launch_comb(*pl, f2(y_pilot), f2(pilots), h, cs(stream))
-                           : launch_lmmse(*pl, f2(y_pilot), f2(pilots), pl->d_w_main, pl->d_w_tail,
-                                          pl->w_main.data(), pl->w_tail.data(), h, cs(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "channel estimator launch");
-  return launched(launch_detect(*pl, h, f2(y_data), f2(x_eq), labels, llr, info, cs(stream)),
-                  "detection kernel launch");
+  return receive_on(reinterpret_cast<const Plan*>(plan), y_pilot, pilots, y_data, h_out, x_eq, labels, llr, info,
+                    cs(stream));
 }
 
 rapro_status rapro_mse_backward(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,

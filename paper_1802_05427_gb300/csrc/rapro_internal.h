@@ -48,6 +48,7 @@ struct Plan {
   float2* d_h_work = nullptr;      // [T][K][M][n_sc] estimate workspace
   int* d_status = nullptr;         // device status word
   void* d_w_tc = nullptr;          // tensor-core filter operand (canonical layout), or null
+  int est_variant = -1;            // estimator kernel (EST_*), -1 = built-in choice; set by rapro_plan_tune
   bool comb = false;               // comb pilot layout (Sec. II)
   std::vector<float2> w_comb;      // comb weights [sets][Q][Q][Q] (3W: 1 set, S-W: K sets)
   float2* d_w_comb = nullptr;
@@ -71,6 +72,11 @@ bool build_comb_weights_fp64(const rapro_params& p, std::vector<double>& w_out);
 cudaError_t launch_comb(const Plan& pl, const float2* y, const float2* pil, float2* h, cudaStream_t st);
 cudaError_t prepare_comb(int device);
 
+// One subframe through the estimator and the detector on st (rapro_receive_subframe).
+rapro_status receive_on(const Plan* pl, const rapro_c32* y_pilot, const rapro_c32* pilots, const rapro_c32* y_data,
+                        rapro_c32* h_out, rapro_c32* x_eq, uint8_t* labels, float* llr, int32_t* info,
+                        cudaStream_t st);
+
 // Reverse mode of the symbol MSE (k_adjoint.cu); weights' chain rule on the host.
 int adjoint_max_block();
 int adjoint_max_subcarriers();
@@ -93,6 +99,11 @@ cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
 cudaError_t prepare_detect(int device);
 cudaError_t prepare_estimate(int device);
 cudaError_t prepare_lmmse_tc(int device);
+// Estimator kernels a plan can use (the autotuner times the ones that apply).
+enum { EST_TC = 0, EST_STREAM = 1, EST_SMALL = 2, EST_TILED = 3, EST_VARIANTS = 4 };
+bool lmmse_variant_ok(const Plan& pl, int v, const float2* x, const float2* pil, const float2* out);
+cudaError_t launch_lmmse_variant(const Plan& pl, int v, const float2* x, const float2* pil, float2* out,
+                                 cudaStream_t st);
 // Tensor-core LS + LMMSE (even B <= 16 dividing n_sc, aligned arrays).
 bool lmmse_tc_shape_ok(const Plan& pl);
 void build_lmmse_tc_weights(const Plan& pl, std::vector<unsigned char>& out);

@@ -38,6 +38,12 @@ class RaproParams(ctypes.Structure):
     ]
 
 
+class RaproJob(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("y_pilot", ctypes.c_void_p), ("pilots", ctypes.c_void_p),
+                ("y_data", ctypes.c_void_p), ("h_out", ctypes.c_void_p), ("x_eq", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("info", ctypes.c_void_p)]
+
+
 class RaproError(RuntimeError):
     def __init__(self, status: int, what: str, msg: str):
         super().__init__(f"{what}: status {status}: {msg}")
@@ -64,6 +70,11 @@ def lib() -> ctypes.CDLL:
         "rapro_build_comb_weights_host": ([ctypes.POINTER(RaproParams), _P], ctypes.c_int),
         "rapro_ce_comb": ([_P, _P, _P, _P, _P], ctypes.c_int),
         "rapro_mse_backward": ([_P] * 12, ctypes.c_int),
+        "rapro_plan_tune": ([_P] * 7, ctypes.c_int),
+        "rapro_plan_variant": ([_P, _P, _P], ctypes.c_int),
+        "rapro_batch_create": ([ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+        "rapro_batch_destroy": ([_P], ctypes.c_int),
+        "rapro_receive_batch": ([_P, ctypes.POINTER(RaproJob), ctypes.c_int, _P], ctypes.c_int),
         "rapro_weight_grad_host": ([ctypes.POINTER(RaproParams), _P, _P, _P], ctypes.c_int),
         "rapro_plan_create": ([ctypes.POINTER(RaproParams), ctypes.POINTER(_P)], ctypes.c_int),
         "rapro_plan_destroy": ([_P], ctypes.c_int),
@@ -269,6 +280,64 @@ def rapro_mse_backward(plan: Plan, y_pilot, pilots, y_data, h, x_eq, x_ref, g_h,
                                     _ptr(g_w_main, (B, B), c64, "g_w_main"),
                                     _ptr(g_w_tail, (tail, tail), c64, "g_w_tail") if tail else None,
                                     _stream(stream)), "rapro_mse_backward")
+
+
+def rapro_plan_tune(plan: Plan, y_pilot, pilots, y_data, h, x_eq, stream=None) -> None:
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    _check(lib().rapro_plan_tune(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
+                                 _ptr(pilots, s["pilots"], c64, "pilots"), _ptr(y_data, s["y_data"], c64, "y_data"),
+                                 _ptr(h, s["h"], c64, "h"), _ptr(x_eq, s["x_eq"], c64, "x_eq"), _stream(stream)),
+           "rapro_plan_tune")
+
+
+def rapro_plan_variant(plan: Plan):
+    """(estimator kernel, detector warps per role) the plan uses."""
+    ev, ds = ctypes.c_int(), ctypes.c_int()
+    _check(lib().rapro_plan_variant(plan.handle, ctypes.byref(ev), ctypes.byref(ds)), "rapro_plan_variant")
+    return ev.value, ds.value
+
+
+class Batch:
+    """A pool of CUDA streams for rapro_receive_batch."""
+
+    def __init__(self, n_streams: int = 8):
+        h = _P()
+        _check(lib().rapro_batch_create(int(n_streams), ctypes.byref(h)), "rapro_batch_create")
+        self.handle = h
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _check(lib().rapro_batch_destroy(self.handle), "rapro_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rapro_receive_batch(batch: Batch, jobs: list, stream=None) -> None:
+    """jobs: dicts with plan (Plan) and the tensors of rapro_receive_subframe
+    (y_pilot, pilots, y_data, x_eq; optional h_out, labels, llr, info)."""
+    import torch
+    arr = (RaproJob * len(jobs))()
+    c64 = torch.complex64
+    for i, j in enumerate(jobs):
+        pl = j["plan"]
+        s = pl.shapes()
+        arr[i].plan = pl.handle.value
+        arr[i].y_pilot = _ptr(j["y_pilot"], s["y_pilot"], c64, "y_pilot").value
+        arr[i].pilots = _ptr(j["pilots"], s["pilots"], c64, "pilots").value
+        arr[i].y_data = _ptr(j["y_data"], s["y_data"], c64, "y_data").value
+        arr[i].x_eq = _ptr(j["x_eq"], s["x_eq"], c64, "x_eq").value
+        for name, shape, dt in (("h_out", s["h"], c64), ("labels", s["labels"], torch.uint8),
+                                ("llr", s["llr"], torch.float32), ("info", s["info"], torch.int32)):
+            v = _ptr(j.get(name), shape, dt, name)
+            setattr(arr[i], name, None if v is None else v.value)
+    _check(lib().rapro_receive_batch(batch.handle, arr, len(jobs), _stream(stream)), "rapro_receive_batch")
 
 
 def rapro_weight_grad_host(p: RaproParams, g_w_main, g_w_tail=None):

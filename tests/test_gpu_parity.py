@@ -540,3 +540,110 @@ def test_autograd_function_and_adam_fit_of_the_channel_statistics():
     assert l_fit < l0 and l_fit <= 1.01 * l_true, (l0, l_fit, l_true)
     for i in range(2):
         assert abs(np.log(float(fit[i] / truth[i]))) < 0.5 * np.log(2.0), (fit, truth)
+
+
+# ----------------------------------------------- batched heterogeneous receive + tuner
+BATCH_JOBS = [
+    # shape, B, layout ("orth" | "comb"), precision
+    (synth.SubframeShape(M=32, K=4, n_sc=72, n_fft=128, snr_db=12.0, qam_bits=2), 12, "orth", R.RAPRO_PREC_FP32),
+    (synth.SubframeShape(M=64, K=8, n_sc=300, n_fft=512, snr_db=18.0, qam_bits=4), 48, "orth", R.RAPRO_PREC_FP32),
+    (synth.SubframeShape(M=128, K=12, n_sc=600, n_fft=1024, snr_db=20.0, qam_bits=6), 12, "orth", R.RAPRO_PREC_FP32),
+    (synth.SubframeShape(M=20, K=16, n_sc=96, n_fft=128, snr_db=25.0, qam_bits=4), 16, "orth", R.RAPRO_PREC_BF16),
+    (synth.SubframeShape(M=40, K=6, n_sc=144, n_fft=256, snr_db=15.0, qam_bits=2), 0, "comb", R.RAPRO_PREC_FP32),
+    (synth.SubframeShape(M=13, K=3, n_sc=75, n_fft=128, snr_db=10.0, qam_bits=2), 10, "orth", R.RAPRO_PREC_FP32),
+]
+
+
+def _batch_job(i, sh, B, layout, prec):
+    if layout == "comb":
+        sf = synth.make_comb_subframe(sh, seed=synth.SEED_BASE + 70 + i, S=12)
+        p = comb_params(sh, 12, R.RAPRO_COMB_SW)
+    else:
+        sf = synth.make_subframe(sh, seed=synth.SEED_BASE + 70 + i)
+        p = params_for(sh, B)
+        p.precision = prec
+    c64 = {k: synth.as_c64(sf[k]) for k in ("y_pilot", "pilots", "y_data")}
+    plan = R.Plan(p)
+    s = plan.shapes()
+    job = dict(plan=plan, y_pilot=_dev(c64["y_pilot"]), pilots=_dev(c64["pilots"]), y_data=_dev(c64["y_data"]),
+               x_eq=torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda"),
+               labels=torch.empty(s["labels"], dtype=torch.uint8, device="cuda"),
+               llr=torch.empty(s["llr"], dtype=torch.float32, device="cuda"),
+               info=torch.full(s["info"], -7, dtype=torch.int32, device="cuda"),
+               h_out=torch.empty(s["h"], dtype=torch.complex64, device="cuda"))
+    if layout == "comb":
+        o = O.comb_receive_subframe(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128),
+                                    c64["y_data"].astype(np.complex128), K=sh.K, S=12, method=O.COMB_SW,
+                                    sigma2=sh.sigma2, r=oracle_r(sh), n_data_per_slot=sh.n_data_per_slot,
+                                    q=sh.qam_bits)
+    else:
+        o = oracle_receive(sh, c64, B)
+    return job, o
+
+
+def _check_job(job, o, sh, prec):
+    h_tol = TOL_BF16 if prec == R.RAPRO_PREC_BF16 else TOL
+    assert rel_err_per(_host(job["h_out"]), o["h"], axes=(2, 3)).max() <= h_tol
+    assert (_host(job["info"]) == 0).all()
+    if prec == R.RAPRO_PREC_FP32:
+        check_detection(dict(x_eq=_host(job["x_eq"]), labels=_host(job["labels"]), llr=_host(job["llr"])), o,
+                        sh.qam_bits)
+
+
+def test_receive_batch_of_uneven_jobs_matches_the_oracle_eager_and_in_a_graph():
+    jobs, refs = [], []
+    for i, (sh, B, layout, prec) in enumerate(BATCH_JOBS):
+        j, o = _batch_job(i, sh, B, layout, prec)
+        jobs.append(j)
+        refs.append(o)
+    batch = R.Batch(4)
+    R.rapro_receive_batch(batch, jobs)
+    torch.cuda.synchronize()
+    for j, o, (sh, B, layout, prec) in zip(jobs, refs, BATCH_JOBS):
+        _check_job(j, o, sh, prec)
+    first = [_host(j["x_eq"]).copy() for j in jobs]
+    for j in jobs:
+        j["x_eq"].zero_()
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            R.rapro_receive_batch(batch, jobs, stream=st)
+    g.replay()
+    torch.cuda.synchronize()
+    for j, x0 in zip(jobs, first):
+        np.testing.assert_array_equal(_host(j["x_eq"]), x0)
+    for j in jobs:
+        assert j["plan"].device_status() == 0
+    shared = dict(jobs[0])
+    shared["h_out"] = None
+    with pytest.raises(R.RaproError):
+        R.rapro_receive_batch(batch, [shared, dict(shared)])
+    batch.close()
+
+
+@pytest.mark.parametrize("case", [(8, 2, 72, 128, 12), (128, 12, 1200, 2048, 12), (64, 8, 300, 512, 48),
+                                  (20, 5, 100, 256, 10)])
+def test_autotuner_picks_an_applicable_kernel_and_keeps_parity(case):
+    M, K, N, nfft, B = case
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=24 if nfft >= 2048 else 6,
+                             tau_rms=8.0 if nfft >= 2048 else 4.0, snr_db=12.0, qam_bits=4)
+    sf, c64 = _inputs(sh, 9)
+    plan = R.Plan(params_for(sh, B))
+    s = plan.shapes()
+    yp, pil, yd = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"])
+    h = torch.empty(s["h"], dtype=torch.complex64, device="cuda")
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+    assert R.rapro_plan_variant(plan)[0] == -1
+    R.rapro_plan_tune(plan, yp, pil, yd, h, x)
+    ev, split = R.rapro_plan_variant(plan)
+    assert ev in (0, 1, 2, 3) and split in (1, 2)
+    if B > 32:
+        assert ev == 3
+    lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
+    llr = torch.empty(s["llr"], dtype=torch.float32, device="cuda")
+    R.rapro_receive_subframe(plan, yp, pil, yd, x, lab, llr, h_out=h)
+    o = oracle_receive(sh, c64, B)
+    assert rel_err_per(_host(h), o["h"], axes=(2, 3)).max() <= TOL
+    check_detection(dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr)), o, sh.qam_bits)
