@@ -34,6 +34,13 @@ struct DetParams {
   int nchunks;
   DetTiles tiles;
   int* status;
+  // FP64 fallback (precision form): subcarriers whose pivot ratio max/min L_jj^2 exceeds
+  // cond_limit, or whose FP32 factorisation failed, are appended to fix_list
+  // (t * N + subcarrier) for the FP64 kernel.
+  int* fix_count;       // null: no fallback
+  int* fix_list;
+  int fix_cap;
+  float cond_limit;
 };
 
 struct DetLaunch {
@@ -408,6 +415,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     // reads the pivot and the column from it (broadcast loads) and updates its own row.
     float inv_l[KT];
     int fail = 0;
+    float dmax = 0.f, dmin = 3.4e38f;        // pivots L_jj^2 of the real users
 #pragma unroll
     for (int j = 0; j < KT; ++j) {
       float2* col = cb + (j & 1) * 16;
@@ -416,6 +424,10 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
       const float d = col[j].x;
       const bool ok = (d > 0.0f) && (d < 3.0e38f);
       if (!ok && fail == 0) fail = j + 1;
+      if (j < K) {
+        dmax = fmaxf(dmax, d);
+        dmin = fminf(dmin, d);
+      }
       const float il = rsqrtf(d);                            // 1 / L_jj
       inv_l[j] = il;
       const float2 lij = make_float2(ar[j].x * il, ar[j].y * il);   // L[i][j] for i > j
@@ -456,6 +468,10 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     }
     if (live) Ss[i * XS + scl] = P.sigma2 * sk;
     if (i == 0) Is[scl] = fail;
+    if (i == 0 && P.fix_count && k0 + scl < N && (fail != 0 || dmax > P.cond_limit * dmin)) {
+      const int slot = atomicAdd(P.fix_count, 1);              // (max L_jj / min L_jj)^2 <= cond(A)
+      if (slot < P.fix_cap) P.fix_list[slot] = t * N + k0 + scl;
+    }
     __syncwarp();
     // w_i = sum_{l <= i} L^-1[i][l] z_l (row i of L^-1 first, then the broadcast z reads).
     float2 yrow[KT], wr[DT];

@@ -65,13 +65,23 @@ static cudaError_t run(DetParams P, const float2* h, const float2* y, float2* x_
 
 cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
                           unsigned char* labels, float* llr, int* info, cudaStream_t st) {
-  DetParams P;
+  DetParams P{};
   P.T = pl.T; P.K = pl.p.K; P.M = pl.p.M; P.N = pl.p.n_sc; P.D = pl.D; P.q = pl.q;
   P.sigma2 = float(pl.p.sigma2);
   P.nchunks = (pl.p.M + DET_MCH - 1) / DET_MCH;
   P.tiles = pl.tiles;
   P.status = pl.d_status;
-  return run(P, h, y, x_eq, labels, llr, info, st);
+  if (pl.d_fix) {
+    P.fix_count = pl.d_fix;
+    P.fix_list = pl.d_fix + 1;
+    P.fix_cap = pl.T * pl.p.n_sc;
+    P.cond_limit = kFp64CondLimit;
+    cudaError_t e = cudaMemsetAsync(pl.d_fix, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = run(P, h, y, x_eq, labels, llr, info, st);
+  if (e != cudaSuccess || !pl.d_fix) return e;
+  return launch_fp64_fix(pl, h, y, x_eq, labels, llr, info, st);
 }
 
 // Detection without a plan (same kernels): used by the allocation-free receive entry point.
@@ -79,7 +89,7 @@ cudaError_t launch_detect_raw(const DetTiles& tiles, int T, int K, int M, int N,
                               float sigma2, int* status, const float2* h, const float2* y,
                               float2* x_eq, unsigned char* labels, float* llr, int* info,
                               cudaStream_t st) {
-  DetParams P;
+  DetParams P{};
   P.T = T; P.K = K; P.M = M; P.N = N; P.D = D; P.q = q;
   P.sigma2 = sigma2;
   P.nchunks = (M + DET_MCH - 1) / DET_MCH;

@@ -450,7 +450,7 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
-    cudaFree(pl->d_w_tc); cudaFree(pl->d_w_comb);
+    cudaFree(pl->d_w_tc); cudaFree(pl->d_w_comb); cudaFree(pl->d_fix);
     delete pl;
     return cuda_fail(err, what);
   };
@@ -471,6 +471,9 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if (pl->tail && (e = cudaMemcpy(pl->d_w_tail, pl->w_tail.data(), pl->w_tail.size() * sizeof(float2),
                                   cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W tail");
   if ((e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset status");
+  if (p->precision == RAPRO_PREC_BF16 &&
+      (e = cudaMalloc(&pl->d_fix, (1 + size_t(pl->T) * p->n_sc) * sizeof(int))) != cudaSuccess)
+    return fail(e, "cudaMalloc FP64-fallback list");
   if (!pl->comb && lmmse_tc_shape_ok(*pl)) {
     std::vector<unsigned char> wtc;
     build_lmmse_tc_weights(*pl, wtc);
@@ -493,6 +496,7 @@ rapro_status rapro_plan_destroy(rapro_plan* plan) {
   cudaFree(pl->d_status);
   cudaFree(pl->d_w_tc);
   cudaFree(pl->d_w_comb);
+  cudaFree(pl->d_fix);
   delete pl;
   return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, "rapro_plan_destroy");
 }

@@ -532,7 +532,7 @@ def test_autograd_function_and_adam_fit_of_the_channel_statistics():
         opt.zero_grad()
         l = AG.symbol_mse(torch.exp(log_theta), batch, shape)
         if l0 is None:
-            l0 = float(l)
+            l0 = float(l.detach())
         l.backward()
         opt.step()
     fit = torch.exp(log_theta.detach())
@@ -647,3 +647,38 @@ def test_autotuner_picks_an_applicable_kernel_and_keeps_parity(case):
     o = oracle_receive(sh, c64, B)
     assert rel_err_per(_host(h), o["h"], axes=(2, 3)).max() <= TOL
     check_detection(dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr)), o, sh.qam_bits)
+
+
+def test_bf16_form_falls_back_to_fp64_on_ill_conditioned_subcarriers():
+    """Users 0 and 1 nearly collinear on two subcarriers with a tiny sigma2: cond(A) ~ 1e8.
+    The precision form re-solves those subcarriers in FP64 (agreeing with the FP64 oracle),
+    where the FP32 detector alone is far off."""
+    sh = synth.SubframeShape(M=16, K=4, n_sc=32, n_fft=64, snr_db=90.0, qam_bits=2)
+    sf, c64 = _inputs(sh, 12)
+    rng = np.random.default_rng(1)
+    h = np.broadcast_to(np.transpose(sf["H"], (1, 0, 2))[None], (sh.n_slots, sh.K, sh.M, sh.n_sc)).copy()
+    bad = [3, 17]
+    for n in bad:
+        h[:, 1, :, n] = h[:, 0, :, n] + 1e-4 * (rng.standard_normal((sh.n_slots, sh.M)) +
+                                                1j * rng.standard_normal((sh.n_slots, sh.M)))
+    h = synth.as_c64(h)
+    x_o, _ = O.mmse_detect(h.astype(np.complex128), c64["y_data"].astype(np.complex128), sh.sigma2,
+                           sh.n_data_per_slot)
+    out = {}
+    for prec in (R.RAPRO_PREC_BF16, R.RAPRO_PREC_FP32):
+        p = params_for(sh, 8)
+        p.precision = prec
+        plan = R.Plan(p)
+        s = plan.shapes()
+        x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+        info = torch.full(s["info"], -7, dtype=torch.int32, device="cuda")
+        R.rapro_mmse_detect(plan, _dev(h), _dev(c64["y_data"]), x, info=info)
+        out[prec] = (_host(x), _host(info))
+    x_b, info_b = out[R.RAPRO_PREC_BF16]
+    assert (info_b == 0).all()
+    e_b = rel_err_per(x_b, x_o, axes=(0, 1))                  # per subcarrier
+    assert e_b[bad].max() <= 1e-5, e_b[bad]
+    good = np.setdiff1d(np.arange(sh.n_sc), bad)
+    assert e_b[good].max() <= 1e-4
+    x_f, _ = out[R.RAPRO_PREC_FP32]
+    assert rel_err_per(x_f, x_o, axes=(0, 1))[bad].min() > 1e-3 or not np.isfinite(x_f[..., bad]).all()
