@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--impl", choices=["rapro", "reference"], default="rapro")
     ap.add_argument("--subblock", type=int, default=12)
     ap.add_argument("--snr", type=float, default=10.0)
-    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip every extra section")
+    ap.add_argument("--sections", default="sweep,precision,differentiable,hetero,comb",
+                    help="extra sections after the headline line's measurement (comma list)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
     return ap.parse_args()
@@ -400,6 +402,9 @@ def run_rapro(args):
         dist.barrier()
     R.lib()
 
+    def want(section):
+        return not args.no_sweep and section in args.sections.split(",")
+
     alg = algorithmic(sh, B)
     res_per_step = alg["res_per_step"]
     params = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, sigma2=sh.sigma2,
@@ -530,7 +535,7 @@ def run_rapro(args):
 
     # sub-block sweep of the same workload (B = 12, 48, 100, 1200), graph replays
     sweep = {}
-    if not args.no_sweep and rank == 0 and world == 1:
+    if want("sweep") and rank == 0 and world == 1:
         for Bs in (12, 48, 100, 1200):
             ps = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=Bs, sigma2=sh.sigma2,
                                qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms)
@@ -559,7 +564,7 @@ def run_rapro(args):
 
     # precision form: the sub-block filter as one BF16 pass on the tensor cores
     prec = {}
-    if not args.no_sweep and rank == 0 and world == 1 and B % 2 == 0 and B <= 16 and sh.n_sc % B == 0:
+    if want("precision") and rank == 0 and world == 1 and B % 2 == 0 and B <= 16 and sh.n_sc % B == 0:
         pb = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, sigma2=sh.sigma2,
                            qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms, precision=R.RAPRO_PREC_BF16)
         with R.Plan(pb) as plb:
@@ -598,7 +603,7 @@ def run_rapro(args):
 
     # differentiable receive: forward + adjoint per subframe, and an Adam fit of (sigma2, tau)
     diff = {}
-    if not args.no_sweep and rank == 0 and world == 1:
+    if want("differentiable") and rank == 0 and world == 1:
         from paper_1802_05427_gb300 import autograd as AG
         shd = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "K": 16, "snr_db": 15.0, "tau_rms": 6.0})
         batch = []
@@ -652,12 +657,12 @@ def run_rapro(args):
 
     # batched heterogeneous receive: 512 subframes of uneven shapes in one call / one graph
     hetero = {}
-    if not args.no_sweep and rank == 0 and world == 1:
+    if want("hetero") and rank == 0 and world == 1:
         hetero = hetero_batch(dev)
 
     # comb pilots (Sec. II, IV-B) on the same 128 x 12 x 1200 shape: 12W, 3W, interpolated LS
     comb = {}
-    if not args.no_sweep and rank == 0 and world == 1:
+    if want("comb") and rank == 0 and world == 1:
         S = 12
         csets = []
         for i in range(N_SETS):

@@ -24,7 +24,8 @@
  *  - No call throws across the ABI, traps on the device or asserts.  NaN/Inf inputs
  *    propagate to the outputs.  Calls that share a plan may run concurrently on
  *    different streams except rapro_receive_subframe with h_out == NULL, which writes
- *    the plan's workspace: serialise those per plan.
+ *    the plan's workspace, and the detector of a RAPRO_PREC_BF16 plan, which keeps its
+ *    FP64-fallback list in the plan: serialise those per plan.
  *
  * Layouts (T = n_pilot_sym slots, D = n_sym / n_pilot_sym - 1 data symbols per slot):
  *   y_pilot, h_ls, h  [T][K][M][n_sc]   pilot observation of user s at antenna m

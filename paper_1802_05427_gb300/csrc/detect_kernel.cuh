@@ -38,9 +38,11 @@ struct DetParams {
   // cond_limit, or whose FP32 factorisation failed, are appended to fix_list
   // (t * N + subcarrier) for the FP64 kernel.
   int* fix_count;       // null: no fallback
+  int* fix_ticket;      // CTAs finished; the last one runs the FP64 solves and resets both
   int* fix_list;
   int fix_cap;
   float cond_limit;
+  double sigma2_d;
 };
 
 struct DetLaunch {
@@ -153,6 +155,12 @@ __device__ __forceinline__ void demap_store(float2 xt, float s, size_t o, unsign
     }
   }
 }
+
+}  // namespace rapro
+
+#include "fixup.cuh"
+
+namespace rapro {
 
 // ------------------------------------------------------------------------ kernel
 template <int KT, int DT, bool USE_TMA>
@@ -304,6 +312,32 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
       __syncthreads();
     }
   }
+  // FP64 fallback (precision form): every CTA counts itself done; the last one re-solves
+  // the flagged subcarriers (process) and clears the list for the next launch.
+  int* s_last = reinterpret_cast<int*>(smem + 136);
+  auto finish_fix = [&](bool process) {
+    if (!P.fix_count) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      *s_last = atomicAdd(P.fix_ticket, 1) == int(gridDim.x * gridDim.y) - 1;
+    }
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    if (process) {
+      const FixArgs fa{h, y, x_eq, labels, llr, info, P.fix_count, P.fix_list, P.fix_cap,
+                       P.T, K, M, N, D, P.q, P.sigma2_d};
+      fp64_fix_items(fa, reinterpret_cast<FixScratch*>(stage0));
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      *P.fix_count = 0;
+      *P.fix_ticket = 0;
+      __threadfence();
+    }
+  };
+
   __syncthreads();
   if (*s_abort) {
     // A pipeline wait ran out: give the copies in flight a bounded chance to land,
@@ -312,6 +346,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
       for (int s = 0; s < DET_STAGES; ++s) (void)mbar_wait_bounded(&full[s], 0);
       atomicExch(P.status, int(RAPRO_ERR_TIMEOUT));
     }
+    finish_fix(false);
     return;
   }
 
@@ -531,6 +566,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     }
   }
   if (info && threadIdx.x < DET_SC && k0 + threadIdx.x < N) info[size_t(t) * N + k0 + threadIdx.x] = Is[threadIdx.x];
+  finish_fix(true);
 }
 
 template <int KT>

@@ -1,16 +1,17 @@
 // FP64 fallback of the precision form: the subcarriers the detector flagged as ill
 // conditioned (pivot ratio (max L_jj / min L_jj)^2 above the limit, a lower bound of
-// cond(A)) are solved again, Eq. 22 in FP64: A = H^H H + sigma2 I and z_d = H^H y_d summed
-// in FP64 from the FP32 inputs, A = L L^H, s_k = sigma2 sum_j |L^-1[j][k]|^2,
-// x~_d = A^-1 z_d; the FP32 outputs (x_eq, labels, LLRs, info) of those subcarriers are
-// overwritten.  One CTA per flagged subcarrier (grid-stride over the device list).
-#include "detect_kernel.cuh"
+// cond(A), or a failed FP32 factorisation) are solved again, Eq. 22 in FP64:
+// A = H^H H + sigma2 I and z_d = H^H y_d summed in FP64 from the FP32 inputs, A = L L^H,
+// s_k = sigma2 sum_j |L^-1[j][k]|^2, x~_d = A^-1 z_d; the FP32 outputs (x_eq, labels, LLRs,
+// info) of those subcarriers are overwritten.  Run by the detector's last CTA to finish.
+#pragma once
+
+#include "rapro_internal.h"
+
+// Included by detect_kernel.cuh after demap_store.
 
 namespace rapro {
 
-namespace {
-
-constexpr int FIX_THREADS = 256;
 constexpr int FIX_MAXK = 16;
 
 struct FixArgs {
@@ -26,15 +27,24 @@ struct FixArgs {
   double sigma2;
 };
 
-__global__ void __launch_bounds__(FIX_THREADS) fp64_fix_kernel(const FixArgs a) {
-  __shared__ double2 A[FIX_MAXK][FIX_MAXK];
-  __shared__ double2 Z[FIX_MAXK][RAPRO_MAX_DATA_PER_SLOT];
-  __shared__ double S[FIX_MAXK];
-  __shared__ int fail_s;
+// Shared scratch of the FP64 solves (16-byte aligned).
+struct FixScratch {
+  double2 A[FIX_MAXK][FIX_MAXK];
+  double2 Z[FIX_MAXK][RAPRO_MAX_DATA_PER_SLOT];
+  double S[FIX_MAXK];
+  int fail;
+};
+
+// Every flagged subcarrier, by all threads of the calling CTA.
+static __device__ __noinline__ void fp64_fix_items(const FixArgs a, FixScratch* sc) {
+  auto& A = sc->A;
+  auto& Z = sc->Z;
+  auto& S = sc->S;
+  int& fail_s = sc->fail;
   const int K = a.K, D = a.D, M = a.M, N = a.N, tid = threadIdx.x;
   const int n_items = min(*a.count, a.cap);
   const int npair = K * (K + 1) / 2;
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  for (int item = 0; item < n_items; ++item) {
     const int code = a.list[item], t = code / N, n = code - t * N;
     // Gram (lower triangle) and matched filter in FP64
     for (int e = tid; e < npair + K * D; e += blockDim.x) {
@@ -141,16 +151,6 @@ __global__ void __launch_bounds__(FIX_THREADS) fp64_fix_kernel(const FixArgs a) 
     if (tid == 0 && a.info) a.info[size_t(t) * N + n] = fail_s;
     __syncthreads();
   }
-}
-
-}  // namespace
-
-cudaError_t launch_fp64_fix(const Plan& pl, const float2* h, const float2* y, float2* x_eq, unsigned char* labels,
-                            float* llr, int* info, cudaStream_t st) {
-  FixArgs a{h, y, x_eq, labels, llr, info, pl.d_fix, pl.d_fix + 1, pl.T * pl.p.n_sc,
-            pl.T, pl.p.K, pl.p.M, pl.p.n_sc, pl.D, pl.q, pl.p.sigma2};
-  fp64_fix_kernel<<<64, FIX_THREADS, 0, st>>>(a);
-  return cudaGetLastError();
 }
 
 }  // namespace rapro

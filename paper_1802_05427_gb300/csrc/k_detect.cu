@@ -71,17 +71,15 @@ cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, floa
   P.nchunks = (pl.p.M + DET_MCH - 1) / DET_MCH;
   P.tiles = pl.tiles;
   P.status = pl.d_status;
-  if (pl.d_fix) {
+  if (pl.d_fix) {                       // [0] count, [1] ticket (both reset by the kernel), [2..] list
     P.fix_count = pl.d_fix;
-    P.fix_list = pl.d_fix + 1;
+    P.fix_ticket = pl.d_fix + 1;
+    P.fix_list = pl.d_fix + 2;
     P.fix_cap = pl.T * pl.p.n_sc;
     P.cond_limit = kFp64CondLimit;
-    cudaError_t e = cudaMemsetAsync(pl.d_fix, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
+    P.sigma2_d = pl.p.sigma2;
   }
-  cudaError_t e = run(P, h, y, x_eq, labels, llr, info, st);
-  if (e != cudaSuccess || !pl.d_fix) return e;
-  return launch_fp64_fix(pl, h, y, x_eq, labels, llr, info, st);
+  return run(P, h, y, x_eq, labels, llr, info, st);
 }
 
 // Detection without a plan (same kernels): used by the allocation-free receive entry point.

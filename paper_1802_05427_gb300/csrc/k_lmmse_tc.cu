@@ -405,9 +405,13 @@ static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil,
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   const size_t smem = tc_smem_bytes<KR, BF>(B);
-  // Resident CTAs per SM: shared memory, threads (2048 per SM) and tensor memory (512 columns).
+  // Resident CTAs per SM: shared memory, threads (2048 per SM), registers (64 K, allocated
+  // per warp in units of 8 per thread) and tensor memory (512 columns).
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, lmmse_tc_kernel<KR, BF>);
+  const int regs_warp = ((std::max(fa.numRegs, 1) + 7) / 8 * 8) * 32;
   int per_sm = int(size_t(smem_sm) / (smem + size_t(reserved)));
-  per_sm = std::max(1, std::min({per_sm, 2048 / TC_THREADS, 512 / (2 * TC_N)}));
+  per_sm = std::max(1, std::min({per_sm, 2048 / TC_THREADS, 512 / (2 * TC_N), 65536 / (regs_warp * (TC_THREADS / 32))}));
   const int grid = std::min(n_tiles, per_sm * sms);
   lmmse_tc_kernel<KR, BF><<<grid, TC_THREADS, smem, st>>>(y, pil, out, M, N, B, n_rb, n_tiles, pl.d_status,
                                                             pl.d_w_tc);

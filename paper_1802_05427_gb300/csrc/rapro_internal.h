@@ -49,7 +49,7 @@ struct Plan {
   int* d_status = nullptr;         // device status word
   void* d_w_tc = nullptr;          // tensor-core filter operand (canonical layout), or null
   int est_variant = -1;            // estimator kernel (EST_*), -1 = built-in choice; set by rapro_plan_tune
-  int* d_fix = nullptr;            // precision form: [1 + T n_sc] FP64-fallback count and list
+  int* d_fix = nullptr;            // precision form: FP64-fallback count, ticket, list [T n_sc]
   bool comb = false;               // comb pilot layout (Sec. II)
   std::vector<float2> w_comb;      // comb weights [sets][Q][Q][Q] (3W: 1 set, S-W: K sets)
   float2* d_w_comb = nullptr;
@@ -100,8 +100,6 @@ cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
 cudaError_t prepare_detect(int device);
 // Precision form: subcarriers with (max L_jj / min L_jj)^2 > kFp64CondLimit are redone in FP64.
 constexpr float kFp64CondLimit = 1.0e6f;
-cudaError_t launch_fp64_fix(const Plan& pl, const float2* h, const float2* y, float2* x_eq, unsigned char* labels,
-                            float* llr, int* info, cudaStream_t st);
 cudaError_t prepare_estimate(int device);
 cudaError_t prepare_lmmse_tc(int device);
 // Estimator kernels a plan can use (the autotuner times the ones that apply).

@@ -471,9 +471,11 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if (pl->tail && (e = cudaMemcpy(pl->d_w_tail, pl->w_tail.data(), pl->w_tail.size() * sizeof(float2),
                                   cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W tail");
   if ((e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset status");
-  if (p->precision == RAPRO_PREC_BF16 &&
-      (e = cudaMalloc(&pl->d_fix, (1 + size_t(pl->T) * p->n_sc) * sizeof(int))) != cudaSuccess)
-    return fail(e, "cudaMalloc FP64-fallback list");
+  if (p->precision == RAPRO_PREC_BF16) {
+    if ((e = cudaMalloc(&pl->d_fix, (2 + size_t(pl->T) * p->n_sc) * sizeof(int))) != cudaSuccess)
+      return fail(e, "cudaMalloc FP64-fallback list");
+    if ((e = cudaMemset(pl->d_fix, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset FP64-fallback count");
+  }
   if (!pl->comb && lmmse_tc_shape_ok(*pl)) {
     std::vector<unsigned char> wtc;
     build_lmmse_tc_weights(*pl, wtc);
