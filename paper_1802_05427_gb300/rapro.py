@@ -396,35 +396,69 @@ def rapro_receive_subframe_noalloc(params: RaproParams, y_pilot, pilots, y_data,
 
 
 class Receiver:
-    """A plan plus device buffers for one subframe: the call a user makes with host data.
+    """A plan plus device buffers for subframes arriving in host memory: the call a user makes.
 
-    ``receive_host`` copies pinned host inputs to the device, runs rapro_receive_subframe
-    and copies the equalised symbols and labels back, all on one stream.
+    ``receive_host`` copies pinned host inputs to the device, runs rapro_receive_subframe and
+    copies the equalised symbols and labels back, all enqueued without waiting.  ``depth``
+    buffer sets on their own streams are used in turn, so the copies of one subframe overlap
+    the kernels of the previous one (the host link, not the kernels, bounds this path).
+    ``join`` makes a stream (default: the current one) wait for everything enqueued so far;
+    host output buffers of subframes still in flight must not be reused before that.
     """
 
-    def __init__(self, params: RaproParams, device: int = 0, want_llr: bool = False):
+    def __init__(self, params: RaproParams, device: int = 0, want_llr: bool = False, depth: int = 2):
         import torch
         torch.cuda.set_device(device)
         self.plan = Plan(params)
         s = self.plan.shapes()
         dev = torch.device("cuda", device)
         self.dev = dev
-        self.y_pilot = torch.empty(s["y_pilot"], dtype=torch.complex64, device=dev)
-        self.pilots = torch.empty(s["pilots"], dtype=torch.complex64, device=dev)
-        self.y_data = torch.empty(s["y_data"], dtype=torch.complex64, device=dev)
-        self.x_eq = torch.empty(s["x_eq"], dtype=torch.complex64, device=dev)
-        self.labels = torch.empty(s["labels"], dtype=torch.uint8, device=dev)
-        self.llr = torch.empty(s["llr"], dtype=torch.float32, device=dev) if want_llr else None
-        self.info = torch.empty(s["info"], dtype=torch.int32, device=dev)
+        self.slots = []
+        for _ in range(max(1, depth)):
+            self.slots.append(dict(
+                y_pilot=torch.empty(s["y_pilot"], dtype=torch.complex64, device=dev),
+                pilots=torch.empty(s["pilots"], dtype=torch.complex64, device=dev),
+                y_data=torch.empty(s["y_data"], dtype=torch.complex64, device=dev),
+                h=torch.empty(s["h"], dtype=torch.complex64, device=dev),
+                x_eq=torch.empty(s["x_eq"], dtype=torch.complex64, device=dev),
+                labels=torch.empty(s["labels"], dtype=torch.uint8, device=dev),
+                llr=torch.empty(s["llr"], dtype=torch.float32, device=dev) if want_llr else None,
+                info=torch.empty(s["info"], dtype=torch.int32, device=dev),
+                stream=torch.cuda.Stream(device=dev)))
+        self._next = 0
+        first = self.slots[0]
+        # single-slot views kept for callers that fill the device buffers themselves
+        self.y_pilot, self.pilots, self.y_data = first["y_pilot"], first["pilots"], first["y_data"]
+        self.x_eq, self.labels, self.llr, self.info = first["x_eq"], first["labels"], first["llr"], first["info"]
 
-    def run_device(self, stream=None) -> None:
-        rapro_receive_subframe(self.plan, self.y_pilot, self.pilots, self.y_data, self.x_eq,
-                               self.labels, self.llr, self.info, stream=stream)
+    def run_device(self, stream=None, slot=None) -> None:
+        sl = self.slots[0] if slot is None else slot
+        rapro_receive_subframe(self.plan, sl["y_pilot"], sl["pilots"], sl["y_data"], sl["x_eq"], sl["labels"],
+                               sl["llr"], sl["info"], h_out=sl["h"], stream=stream)
 
-    def receive_host(self, y_pilot_h, pilots_h, y_data_h, x_eq_h, labels_h, stream=None) -> None:
-        self.y_pilot.copy_(y_pilot_h, non_blocking=True)
-        self.pilots.copy_(pilots_h, non_blocking=True)
-        self.y_data.copy_(y_data_h, non_blocking=True)
-        self.run_device(stream)
-        x_eq_h.copy_(self.x_eq, non_blocking=True)
-        labels_h.copy_(self.labels, non_blocking=True)
+    def fork(self, stream=None) -> None:
+        """Every slot stream waits for ``stream`` (default: the current stream)."""
+        import torch
+        src = torch.cuda.current_stream(self.dev) if stream is None else stream
+        for sl in self.slots:
+            sl["stream"].wait_stream(src)
+
+    def join(self, stream=None) -> None:
+        """``stream`` (default: the current stream) waits for every slot stream."""
+        import torch
+        dst = torch.cuda.current_stream(self.dev) if stream is None else stream
+        for sl in self.slots:
+            dst.wait_stream(sl["stream"])
+
+    def receive_host(self, y_pilot_h, pilots_h, y_data_h, x_eq_h, labels_h) -> None:
+        import torch
+        sl = self.slots[self._next]
+        self._next = (self._next + 1) % len(self.slots)
+        st = sl["stream"]
+        with torch.cuda.stream(st):
+            sl["y_pilot"].copy_(y_pilot_h, non_blocking=True)
+            sl["pilots"].copy_(pilots_h, non_blocking=True)
+            sl["y_data"].copy_(y_data_h, non_blocking=True)
+            self.run_device(st, sl)
+            x_eq_h.copy_(sl["x_eq"], non_blocking=True)
+            labels_h.copy_(sl["labels"], non_blocking=True)

@@ -682,3 +682,30 @@ def test_bf16_form_falls_back_to_fp64_on_ill_conditioned_subcarriers():
     assert e_b[good].max() <= 1e-4
     x_f, _ = out[R.RAPRO_PREC_FP32]
     assert rel_err_per(x_f, x_o, axes=(0, 1))[bad].min() > 1e-3 or not np.isfinite(x_f[..., bad]).all()
+
+
+def test_receiver_pipelines_host_subframes_correctly():
+    """Receiver.receive_host with two buffer sets in flight: every subframe's results match
+    the oracle (the overlap of copies and kernels changes no result)."""
+    sh = synth.SubframeShape(M=32, K=4, n_sc=120, n_fft=256, snr_db=15.0, qam_bits=4)
+    rx = R.Receiver(params_for(sh, 12), depth=2)
+    s = rx.plan.shapes()
+    subframes, outs = [], []
+    for i in range(4):
+        sf, c64 = _inputs(sh, synth.SEED_BASE + 80 + i)
+        subframes.append(c64)
+        host = {k: torch.from_numpy(c64[k]).pin_memory() for k in ("y_pilot", "pilots", "y_data")}
+        x_h = torch.empty(s["x_eq"], dtype=torch.complex64).pin_memory()
+        lab_h = torch.empty(s["labels"], dtype=torch.uint8).pin_memory()
+        outs.append((host, x_h, lab_h))
+    rx.fork()
+    for host, x_h, lab_h in outs:
+        rx.receive_host(host["y_pilot"], host["pilots"], host["y_data"], x_h, lab_h)
+    rx.join()
+    torch.cuda.synchronize()
+    for c64, (_, x_h, lab_h) in zip(subframes, outs):
+        o = oracle_receive(sh, c64, 12)
+        assert rel_err_per(x_h.numpy(), o["x_eq"], axes=(2,)).max() <= TOL
+        margin = O.boundary_margin(o["xhat"], sh.qam_bits)
+        far = margin > MARGIN
+        assert (lab_h.numpy()[far] == o["labels"][far]).all()
