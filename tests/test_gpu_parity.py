@@ -709,3 +709,47 @@ def test_receiver_pipelines_host_subframes_correctly():
         margin = O.boundary_margin(o["xhat"], sh.qam_bits)
         far = margin > MARGIN
         assert (lab_h.numpy()[far] == o["labels"][far]).all()
+
+
+def test_new_entry_points_reject_bad_arguments():
+    """Argument checks of the comb, adjoint, tuner and batch entry points (no launch)."""
+    sh = synth.TINY
+    orth = R.Plan(params_for(sh, 12))
+    comb = R.Plan(comb_params(sh, 6, R.RAPRO_COMB_3W))
+    so, sc = orth.shapes(), comb.shapes()
+    z = lambda shape, dt=torch.complex64: torch.zeros(shape, dtype=dt, device="cuda")
+    # the adjoint reads the orthogonal layout
+    with pytest.raises(R.RaproError) as e:
+        R.rapro_mse_backward(comb, z(sc["y_pilot"]), z(sc["pilots"]), z(sc["y_data"]), z(sc["h"]), z(sc["x_eq"]),
+                             z(sc["x_eq"]), z(sc["h"]), z((2,), torch.float32), z((0, 0)))
+    assert e.value.status in (R.RAPRO_ERR_UNSUPPORTED, R.RAPRO_ERR_INVALID_ARG)
+    # the adjoint supports B <= 64
+    big = R.Plan(params_for(synth.SubframeShape(M=4, K=2, n_sc=72, n_fft=128), 72))
+    sb = big.shapes()
+    with pytest.raises(R.RaproError) as e:
+        R.rapro_mse_backward(big, z(sb["y_pilot"]), z(sb["pilots"]), z(sb["y_data"]), z(sb["h"]), z(sb["x_eq"]),
+                             z(sb["x_eq"]), z(sb["h"]), z((2,), torch.float32), z((72, 72)))
+    assert e.value.status == R.RAPRO_ERR_UNSUPPORTED
+    # g_h must not alias an input
+    h = z(so["h"])
+    with pytest.raises(R.RaproError) as e:
+        R.rapro_mse_backward(orth, z(so["y_pilot"]), z(so["pilots"]), z(so["y_data"]), h, z(so["x_eq"]),
+                             z(so["x_eq"]), h, z((2,), torch.float32), z((12, 12)))
+    assert e.value.status == R.RAPRO_ERR_INVALID_ARG
+    # the weight gradient covers the exponential model only
+    pu = params_for(sh, 12, pdp="uniform_L")
+    with pytest.raises(R.RaproError):
+        R.rapro_weight_grad_host(pu, np.zeros((12, 12), np.complex128))
+    # batch: a pool of 0 or 33 streams, a job without arrays
+    for n in (0, 33):
+        with pytest.raises(R.RaproError):
+            R.Batch(n)
+    b = R.Batch(2)
+    arr = (R.RaproJob * 1)()
+    arr[0].plan = orth.handle.value
+    with pytest.raises(R.RaproError):
+        R._check(R.lib().rapro_receive_batch(b.handle, arr, 1, None), "rapro_receive_batch")
+    assert R.lib().rapro_receive_batch(b.handle, None, 0, None) == R.RAPRO_OK
+    b.close()
+    # the tuner needs every array
+    assert R.lib().rapro_plan_tune(orth.handle, None, None, None, None, None, None) == R.RAPRO_ERR_INVALID_ARG
