@@ -163,7 +163,9 @@ __device__ __forceinline__ void demap_store(float2 xt, float s, size_t o, unsign
 namespace rapro {
 
 // ------------------------------------------------------------------------ kernel
-template <int KT, int DT, bool USE_TMA>
+// FIX: the FP64 fallback of the precision form is compiled in (flagging and the last CTA's
+// solves); without it the FP32 path carries none of that code.
+template <int KT, int DT, bool USE_TMA, bool FIX>
 __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     detect_kernel(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_y,
                   const float2* __restrict__ h, const float2* __restrict__ y,
@@ -316,6 +318,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   // the flagged subcarriers (process) and clears the list for the next launch.
   int* s_last = reinterpret_cast<int*>(smem + 136);
   auto finish_fix = [&](bool process) {
+    if constexpr (!FIX) return;
     if (!P.fix_count) return;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     }
     if (live) Ss[i * XS + scl] = P.sigma2 * sk;
     if (i == 0) Is[scl] = fail;
-    if (i == 0 && P.fix_count && k0 + scl < N && (fail != 0 || dmax > P.cond_limit * dmin)) {
+    if (FIX && i == 0 && P.fix_count && k0 + scl < N && (fail != 0 || dmax > P.cond_limit * dmin)) {
       const int slot = atomicAdd(P.fix_count, 1);              // (max L_jj / min L_jj)^2 <= cond(A)
       if (slot < P.fix_cap) P.fix_list[slot] = t * N + k0 + scl;
     }
@@ -590,29 +593,37 @@ template <> cudaError_t detect_prepare_kt<16>(int smem);
   template <>                                                                                          \
   cudaError_t detect_launch_kt<KTV>(const DetLaunch& L) {                                              \
     dim3 grid((L.P.N + DET_SC - 1) / DET_SC, L.P.T);                                                   \
-    dim3 block(det_block_threads(L.P.tiles));                                                                \
-    const bool d12 = L.P.D > 6;                                                                        \
-    if (L.tma) {                                                                                       \
-      if (d12) detect_kernel<KTV, 12, true><<<grid, block, L.smem, L.stream>>>(                        \
-          L.map_h, L.map_y, L.h, L.y, L.x_eq, L.labels, L.llr, L.info, L.P);                           \
-      else detect_kernel<KTV, 6, true><<<grid, block, L.smem, L.stream>>>(                             \
-          L.map_h, L.map_y, L.h, L.y, L.x_eq, L.labels, L.llr, L.info, L.P);                           \
-    } else {                                                                                           \
-      if (d12) detect_kernel<KTV, 12, false><<<grid, block, L.smem, L.stream>>>(                       \
-          L.map_h, L.map_y, L.h, L.y, L.x_eq, L.labels, L.llr, L.info, L.P);                           \
-      else detect_kernel<KTV, 6, false><<<grid, block, L.smem, L.stream>>>(                            \
-          L.map_h, L.map_y, L.h, L.y, L.x_eq, L.labels, L.llr, L.info, L.P);                           \
+    dim3 block(det_block_threads(L.P.tiles));                                                          \
+    const int v = (L.P.D > 6 ? 1 : 0) + (L.tma ? 2 : 0) + (L.P.fix_count ? 4 : 0);                    \
+    switch (v) {                                                                                       \
+      case 0: RAPRO_DETECT_GO(KTV, 6, false, false); break;                                            \
+      case 1: RAPRO_DETECT_GO(KTV, 12, false, false); break;                                           \
+      case 2: RAPRO_DETECT_GO(KTV, 6, true, false); break;                                             \
+      case 3: RAPRO_DETECT_GO(KTV, 12, true, false); break;                                            \
+      case 4: RAPRO_DETECT_GO(KTV, 6, false, true); break;                                             \
+      case 5: RAPRO_DETECT_GO(KTV, 12, false, true); break;                                            \
+      case 6: RAPRO_DETECT_GO(KTV, 6, true, true); break;                                              \
+      default: RAPRO_DETECT_GO(KTV, 12, true, true); break;                                            \
     }                                                                                                  \
     return cudaGetLastError();                                                                         \
   }                                                                                                    \
   template <>                                                                                          \
   cudaError_t detect_prepare_kt<KTV>(int smem) {                                                       \
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;                           \
-    cudaError_t e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true>, A, smem);                        \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true>, A, smem);             \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, false>, A, smem);             \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, false>, A, smem);            \
+    cudaError_t e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true, false>, A, smem);                 \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true, false>, A, smem);      \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, false, false>, A, smem);      \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, false, false>, A, smem);     \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true, true>, A, smem);        \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true, true>, A, smem);       \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, false, true>, A, smem);       \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, false, true>, A, smem);      \
     return e;                                                                                          \
   }
+
+#define RAPRO_DETECT_GO(KTV, DTV, TMA, FIXV)                                                            \
+  detect_kernel<KTV, DTV, TMA, FIXV><<<grid, block, L.smem, L.stream>>>(L.map_h, L.map_y, L.h, L.y,    \
+                                                                        L.x_eq, L.labels, L.llr,       \
+                                                                        L.info, L.P)
 
 }  // namespace rapro
