@@ -113,6 +113,20 @@ typedef enum {
   RAPRO_PREC_BF16 = 1
 } rapro_precision;
 
+/* How rapro_receive_subframe runs a subframe (no counterpart in the paper, which runs the
+ * steps one after the other on each core; the results agree to FP32 rounding). */
+typedef enum {
+  /* Default: the estimator kernel (into h_out or the plan's workspace), then the detector. */
+  RAPRO_RECV_SPLIT = 0,
+  /* One kernel does LS (Eq. 9), the sub-block LMMSE (Eq. 12, FP32 FMAs) and the detection
+   * (Eq. 20-22) per tile of 16 subcarriers, the estimate of each antenna chunk staying in
+   * shared memory (written to h_out only if given).  Applies to orthogonal-layout
+   * RAPRO_PREC_FP32 plans with an even B <= 16, even n_sc and 16-byte aligned y_pilot and
+   * y_data; other plans and arrays take the two-kernel form.  Faster than the default on
+   * small subframes (one launch) and some block sizes; rapro_plan_tune picks the faster. */
+  RAPRO_RECV_FUSED = 1
+} rapro_receive_form;
+
 #define RAPRO_MAX_PILOT_SYM 8
 #define RAPRO_MAX_USERS 16       /* K limit of the register-tiled detector */
 #define RAPRO_MAX_DATA_PER_SLOT 12
@@ -255,9 +269,11 @@ rapro_status rapro_ce_comb(const rapro_plan* plan, const rapro_c32* y_pilot, con
                            rapro_c32* h, rapro_stream stream);
 
 /*
- * The whole path (a1, a3, a4-a8) for one subframe: rapro_ce_ls_lmmse (rapro_ce_comb for a
- * comb plan), then rapro_mmse_detect, on the same stream.  h_out (nullable) receives the
- * channel estimate; when NULL the plan's workspace holds it.  Other arguments as above.
+ * The whole path (a1, a3, a4-a8) for one subframe on one stream, in the plan's receive form
+ * (rapro_receive_form): fused into one kernel where it applies, else rapro_ce_ls_lmmse
+ * (rapro_ce_comb for a comb plan) followed by rapro_mmse_detect.  h_out (nullable)
+ * receives the channel estimate; when NULL the two-kernel form keeps it in the plan's
+ * workspace and the fused form does not store it.  Other arguments as above.
  */
 rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_pilot,
                                     const rapro_c32* pilots, const rapro_c32* y_data,
@@ -268,9 +284,11 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
  * Autotuner (no counterpart in the paper, whose receiver has one code path): times every
  * estimator kernel that applies to the plan's shape and these arrays (tensor cores,
  * streaming, row-segment and tiled kernels; comb plans have one) and the detector's
- * warps-per-role split, 2 warm and 5 timed launches each on the caller's stream, and keeps
- * the fastest in the plan (later calls with arrays the choice does not apply to fall back
- * to the built-in choice).  Overwrites h and x_eq.  Synchronises the stream; not inside a
+ * warps-per-role split, then (where it applies to these arrays) the fused receive form with
+ * each split against the tuned two-kernel form, 2 warm and 5 timed launches each on the
+ * caller's stream, and keeps the fastest in the plan: estimator, split and receive form
+ * (later calls with arrays a choice does not apply to fall back to the built-in choice).
+ * Overwrites h and x_eq.  Synchronises the stream; not inside a
  * stream capture.  The plan must not be in use by another stream meanwhile.
  */
 rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
@@ -279,6 +297,15 @@ rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const r
 /* The plan's kernel choices: estimator kernel (-1 built-in, 0 tensor cores, 1 streaming,
  * 2 row segments, 3 tiled) and the detector's warps per role.  Either pointer may be NULL. */
 rapro_status rapro_plan_variant(const rapro_plan* plan, int* est_variant, int* det_split);
+
+/* Set the plan's receive form (rapro_receive_form; RAPRO_ERR_INVALID_ARG otherwise).  Not
+ * while another stream uses the plan. */
+rapro_status rapro_plan_set_receive_form(rapro_plan* plan, int form);
+
+/* *fused = 1 if rapro_receive_subframe with these y_pilot and y_data pointers runs the fused
+ * kernel under the plan's current form, else 0.  No device work. */
+rapro_status rapro_receive_is_fused(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* y_data,
+                                    int* fused);
 
 /*
  * Batched heterogeneous receive: many independent subframes, each with its own plan (any

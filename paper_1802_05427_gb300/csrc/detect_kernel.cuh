@@ -19,6 +19,15 @@
 //   s_i = sigma2 [A^-1]_ii = sigma2 sum_j |L^-1[j][i]|^2; w = L^-1 z lane-per-row and
 //   x~ = L^-H w lane-per-column.
 // Then all threads demap (x^ = x~ / mu, mu = 1 - s) and store with coalesced writes.
+//
+// Fused receive form (DET_FUSED): the CTA takes the raw pilot symbols instead of h.  Each
+// stage then holds y_pilot for the tile's LMMSE blocks (K users x 8 antennas x `span`
+// subcarriers from the first block's start) besides the data symbols; consumer half-warps
+// filter the chunk, lane = output subcarrier, with the LS division folded into the lane's
+// weight row (h_j = sum_i W[j][i] conj(p_i) / |p_i|^2 y_i, Eq. 9 and 12), write h into a
+// double-buffered chunk of shared memory, meet at a named barrier and run the Gram and
+// matched filter on it as above.  The estimate never leaves the SM (unless the caller asks
+// for it), and the subframe needs one launch.
 #pragma once
 
 #include <cudaTypedefs.h>
@@ -43,7 +52,17 @@ struct DetParams {
   int fix_cap;
   float cond_limit;
   double sigma2_d;
+  // Fused receive form: map_h covers y_pilot [T K][M][N] in boxes of span x DET_MCH x K.
+  const float2* pil;      // pilots [T][K][N]
+  const float2* w_main;   // W of a full block [B][B], row-major (h_j = sum_i W[j][i] h_ls_i)
+  const float2* w_tail;   // W of the tail block [tail][tail], or null
+  float2* h_out;          // channel estimate [T][K][M][N], or null (then not written)
+  int B, nfull, tail;     // block size, full blocks, tail block length
+  int span, nst;          // pilot box width in subcarriers, stage ring depth
 };
+
+// Kernel forms: plain detection, detection with the FP64 fallback, fused receive.
+enum { DET_PLAIN = 0, DET_FIX = 1, DET_FUSED = 2 };
 
 struct DetLaunch {
   CUtensorMap map_h, map_y;
@@ -55,6 +74,7 @@ struct DetLaunch {
   int* info;
   DetParams P;
   bool tma;
+  bool fused;
   size_t smem;
   cudaStream_t stream;
 };
@@ -94,6 +114,14 @@ __host__ __device__ constexpr size_t det_scratch_bytes(int KT, int DT) {
 
 inline size_t det_stage_bytes(const DetTiles& t) {
   return size_t(t.KP + t.DP) * DET_MCH * DET_SC * sizeof(float2);
+}
+
+// Fused form, in float2 units after the 1 KB header: the ring [nst][K*DET_MCH*span +
+// DP*DET_MCH*DET_SC], the filtered chunk [2][KP][DET_MCH][DET_SC], the LS-folded weights
+// [K][DET_SC][16] (zero past each block's length).
+inline size_t fused_work_bytes(const DetTiles& t, int K, int span, int nst) {
+  const size_t stage = size_t(K) * DET_MCH * span + size_t(t.DP) * DET_MCH * DET_SC;
+  return (size_t(nst) * stage + 2 * size_t(t.KP) * DET_MCH * DET_SC + size_t(K) * DET_SC * 16) * sizeof(float2);
 }
 
 // --------------------------------------------------------------- demapper helpers
@@ -163,14 +191,18 @@ __device__ __forceinline__ void demap_store(float2 xt, float s, size_t o, unsign
 namespace rapro {
 
 // ------------------------------------------------------------------------ kernel
-// FIX: the FP64 fallback of the precision form is compiled in (flagging and the last CTA's
-// solves); without it the FP32 path carries none of that code.
-template <int KT, int DT, bool USE_TMA, bool FIX>
+// MODE DET_FIX compiles in the FP64 fallback of the precision form (flagging and the last
+// CTA's solves), so the FP32 path carries none of that code; DET_FUSED is the fused
+// receive form (TMA only).
+template <int KT, int DT, bool USE_TMA, int MODE>
 __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     detect_kernel(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_y,
                   const float2* __restrict__ h, const float2* __restrict__ y,
                   float2* __restrict__ x_eq, unsigned char* __restrict__ labels,
                   float* __restrict__ llr, int* __restrict__ info, const __grid_constant__ DetParams P) {
+  constexpr bool FIX = MODE == DET_FIX;
+  constexpr bool FUSED = MODE == DET_FUSED;
+  static_assert(!FUSED || USE_TMA, "the fused form streams through TMA");
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   int* s_abort = reinterpret_cast<int*>(smem + 128);
@@ -181,18 +213,28 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   const int t = blockIdx.y, k0 = blockIdx.x * DET_SC;
   const int K = P.K, D = P.D, M = P.M, N = P.N;
   const int KP = P.tiles.KP, DP = P.tiles.DP;
-  const int stage_elems = (KP + DP) * DET_MCH * DET_SC;
-  const int nst = USE_TMA ? DET_STAGES : 1;
+  constexpr int PL = DET_MCH * DET_SC;                 // one operand row of a stage
+  const int span = FUSED ? P.span : 0;
+  const int yoff = FUSED ? K * DET_MCH * span : KP * PL;        // data rows within a stage
+  const int stage_elems = yoff + DP * PL;
+  const int nst = USE_TMA ? (FUSED ? P.nst : DET_STAGES) : 1;
+  float2* hs = stage0 + size_t(nst) * stage_elems;     // fused: filtered chunk [2][KP][PL]
+  float2* wps = hs + 2 * KP * PL;                      // fused: weights [K][DET_SC][16]
+  const int x0 = FUSED ? (k0 / P.B) * P.B : k0;        // first subcarrier of a pilot box
 
   // Zero the padding rows (users K..KP-1, symbols D..DP-1) of every stage once; the
-  // loads never write them.
+  // loads never write them.  (Fused: the user padding lives in the filtered chunk.)
   for (int s = 0; s < nst; ++s) {
     float2* st = stage0 + s * stage_elems;
-    for (int e = threadIdx.x; e < (KP - K) * DET_MCH * DET_SC; e += blockDim.x)
-      st[K * DET_MCH * DET_SC + e] = make_float2(0.f, 0.f);
-    for (int e = threadIdx.x; e < (DP - D) * DET_MCH * DET_SC; e += blockDim.x)
-      st[(KP + D) * DET_MCH * DET_SC + e] = make_float2(0.f, 0.f);
+    if (!FUSED)
+      for (int e = threadIdx.x; e < (KP - K) * PL; e += blockDim.x) st[K * PL + e] = make_float2(0.f, 0.f);
+    for (int e = threadIdx.x; e < (DP - D) * PL; e += blockDim.x) st[yoff + D * PL + e] = make_float2(0.f, 0.f);
   }
+  if (FUSED)
+    for (int e = threadIdx.x; e < 2 * (KP - K) * PL; e += blockDim.x) {
+      const int b = e / ((KP - K) * PL), r = e % ((KP - K) * PL);
+      hs[b * KP * PL + K * PL + r] = make_float2(0.f, 0.f);
+    }
   // Consumer warps (one or two per role) and, on the TMA path, one producer warp (the last).
   const int n_cons = P.tiles.n_roles * P.tiles.msplit;
   uint64_t* full = bars;                      // [DET_STAGES] TMA bytes landed
@@ -209,22 +251,22 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   }
   __syncthreads();
 
-  const uint32_t stage_tx = uint32_t((K + D) * DET_MCH * DET_SC * sizeof(float2));
+  const uint32_t stage_tx = uint32_t((FUSED ? K * DET_MCH * span + D * PL : (K + D) * PL) * sizeof(float2));
   if (USE_TMA && warp == n_cons) {
     // Producer: stream every antenna chunk through the stage ring.
     if (lane == 0) {
       prefetch_tensormap(&map_h);
       prefetch_tensormap(&map_y);
       for (int c = 0; c < P.nchunks; ++c) {
-        const int s = c % DET_STAGES;
-        if (c >= DET_STAGES && !mbar_wait_bounded(&empty[s], uint32_t(c / DET_STAGES - 1) & 1u)) {
+        const int s = c % nst;
+        if (c >= nst && !mbar_wait_bounded(&empty[s], uint32_t(c / nst - 1) & 1u)) {
           atomicExch(s_abort, 1);
           break;
         }
         float2* st = stage0 + s * stage_elems;
         mbar_arrive_expect_tx(&full[s], stage_tx);
-        tma_load_3d(st, &map_h, &full[s], k0, c * DET_MCH, t * K);
-        tma_load_3d(st + KP * DET_MCH * DET_SC, &map_y, &full[s], k0, c * DET_MCH, t * D);
+        tma_load_3d(st, &map_h, &full[s], x0, c * DET_MCH, t * K);
+        tma_load_3d(st + yoff, &map_y, &full[s], k0, c * DET_MCH, t * D);
       }
     }
     __syncwarp();
@@ -237,18 +279,57 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   const int sc = lane & 15, mh = lane >> 4;
   const int per = DET_MCH / (2 * P.tiles.msplit);      // antennas of a chunk per half-warp
   const int m_first = (mg * 2 + mh) * per;
-  constexpr int PL = DET_MCH * DET_SC;                 // one operand row of a stage
   float2 acc[26];
 #pragma unroll
   for (int e = 0; e < 26; ++e) acc[e] = make_float2(0.f, 0.f);
 
   const bool consumer = warp < n_cons;
+  // Fused form: the LS-folded weights of the tile, wps[k][j][i] = W[j'][i] conj(p_i) / |p_i|^2
+  // for output subcarrier k0 + j at position j' of its block (zero past the block's length
+  // and past n_sc), and each lane's input offset within the pilot box.
+  int off_j = 0;
+  if constexpr (FUSED) {
+    if (consumer) {
+      for (int e = threadIdx.x; e < K * DET_SC * 16; e += n_cons * 32) {
+        const int k = e >> 8, j = (e >> 4) & 15, i = e & 15;
+        const int kg = k0 + j;
+        float2 v = make_float2(0.f, 0.f);
+        if (kg < N) {
+          const int b = kg / P.B, jp = kg - b * P.B;
+          const bool full_blk = b < P.nfull;
+          if (i < (full_blk ? P.B : P.tail)) {
+            const float2 w = full_blk ? P.w_main[jp * P.B + i] : P.w_tail[jp * P.tail + i];
+            const float2 pl = P.pil[size_t(t * K + k) * N + b * P.B + i];
+            const float inv = 1.0f / fmaf(pl.x, pl.x, pl.y * pl.y);
+            v = make_float2(fmaf(w.x, pl.x, w.y * pl.y) * inv, fmaf(w.y, pl.x, -w.x * pl.y) * inv);
+          }
+        }
+        wps[e] = v;
+      }
+      if (k0 + sc < N) off_j = ((k0 + sc) / P.B) * P.B - x0;
+      named_bar_sync(1, n_cons * 32);
+    }
+  }
+  float2 wp[16];                                       // fused: weight row of user cur_k
+  int cur_k = -1;
+  bool aborted = false;
+
   for (int c = 0; c < P.nchunks; ++c) {
-    const int s = USE_TMA ? (c % DET_STAGES) : 0;
+    const int s = USE_TMA ? (c % nst) : 0;
     float2* st = stage0 + s * stage_elems;
     if (USE_TMA) {
       if (!consumer) break;
-      if (!mbar_wait_bounded(&full[s], uint32_t(c / DET_STAGES) & 1u)) {
+      if constexpr (FUSED) {
+        // Every consumer warp passes the named barrier of every chunk, so a wait that ran
+        // out marks the warp aborted instead of leaving the loop.
+        bool ok = !aborted && !*reinterpret_cast<volatile int*>(s_abort) &&
+                  mbar_wait_bounded(&full[s], uint32_t(c / nst) & 1u);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          if (!aborted && lane == 0) atomicExch(s_abort, 1);
+          aborted = true;
+        }
+      } else if (!mbar_wait_bounded(&full[s], uint32_t(c / nst) & 1u)) {
         atomicExch(s_abort, 1);
         break;
       }
@@ -266,8 +347,57 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
       }
       __syncthreads();
     }
-    if (consumer) {
-      const float2* sl = st + sc;
+    const float2* hsrc = st;                           // the chunk's h rows [KP][PL]
+    if constexpr (FUSED) {
+      // LS + LMMSE of the chunk: half-warp g takes units u = (user u/2, antenna parity u%2)
+      // of 4 rows; lane sc owns output subcarrier k0 + sc.  The two half-warps of a warp
+      // read adjacent rows, which sit on different banks (span % 16 != 0).
+      float2* hb = hs + (c & 1) * KP * PL;
+      if (!aborted) {
+        for (int u = warp * 2 + mh; u < 2 * K; u += 2 * n_cons) {
+          const int k = u >> 1, par = u & 1;
+          if (k != cur_k) {
+            const float4* wr = reinterpret_cast<const float4*>(wps + (k * DET_SC + sc) * 16);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float4 v = wr[i];
+              wp[2 * i] = make_float2(v.x, v.y);
+              wp[2 * i + 1] = make_float2(v.z, v.w);
+            }
+            cur_k = k;
+          }
+          float2 a[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) a[r] = make_float2(0.f, 0.f);
+          const float2* src = st + (k * DET_MCH + par) * span + off_j;
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            if (i < P.B) {
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const float4 v = *reinterpret_cast<const float4*>(src + 2 * r * span + i);
+                cmac(a[r], wp[i], make_float2(v.x, v.y));
+                cmac(a[r], wp[i + 1], make_float2(v.z, v.w));
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int m = par + 2 * r;
+            hb[k * PL + m * DET_SC + sc] = a[r];
+            if (P.h_out) {
+              const int mgl = c * DET_MCH + m, kg = k0 + sc;
+              if (kg < N && mgl < M) P.h_out[(size_t(t * K + k) * M + mgl) * N + kg] = a[r];
+            }
+          }
+        }
+      }
+      named_bar_sync(1, n_cons * 32);
+      hsrc = hb;
+    }
+    if (consumer && !aborted) {
+      const float2* sl = hsrc + sc;
+      const float2* yl = st + yoff + sc;
 #pragma unroll
       for (int mm = 0; mm < DET_MCH / 2; ++mm) {
         if (mm < per) {
@@ -277,7 +407,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii) a4[ii] = sl[(4 * rg + ii) * PL + mo];
 #pragma unroll
-            for (int jj = 0; jj < 6; ++jj) y6[jj] = sl[(KP + 6 * rc + jj) * PL + mo];
+            for (int jj = 0; jj < 6; ++jj) y6[jj] = yl[(6 * rc + jj) * PL + mo];
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
@@ -309,7 +439,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     }
     if (USE_TMA) {
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);          // this warp is done with the stage
+      if (lane == 0 && !aborted) mbar_arrive(&empty[s]);   // this warp is done with the stage
     } else {
       __syncthreads();
     }
@@ -346,7 +476,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     // A pipeline wait ran out: give the copies in flight a bounded chance to land,
     // record the timeout and leave without touching the outputs.
     if (threadIdx.x == 0) {
-      for (int s = 0; s < DET_STAGES; ++s) (void)mbar_wait_bounded(&full[s], 0);
+      for (int s = 0; s < nst; ++s) (void)mbar_wait_bounded(&full[s], 0);
       atomicExch(P.status, int(RAPRO_ERR_TIMEOUT));
     }
     finish_fix(false);
@@ -576,17 +706,17 @@ template <int KT>
 cudaError_t detect_launch_kt(const DetLaunch& L);
 
 template <int KT>
-cudaError_t detect_prepare_kt(int smem);
+cudaError_t detect_prepare_kt(int smem, int fused_smem);
 
 // One explicit specialisation per padded user count, each in its own translation unit.
 template <> cudaError_t detect_launch_kt<4>(const DetLaunch& L);
 template <> cudaError_t detect_launch_kt<8>(const DetLaunch& L);
 template <> cudaError_t detect_launch_kt<12>(const DetLaunch& L);
 template <> cudaError_t detect_launch_kt<16>(const DetLaunch& L);
-template <> cudaError_t detect_prepare_kt<4>(int smem);
-template <> cudaError_t detect_prepare_kt<8>(int smem);
-template <> cudaError_t detect_prepare_kt<12>(int smem);
-template <> cudaError_t detect_prepare_kt<16>(int smem);
+template <> cudaError_t detect_prepare_kt<4>(int smem, int fused_smem);
+template <> cudaError_t detect_prepare_kt<8>(int smem, int fused_smem);
+template <> cudaError_t detect_prepare_kt<12>(int smem, int fused_smem);
+template <> cudaError_t detect_prepare_kt<16>(int smem, int fused_smem);
 
 // Definitions, instantiated once per KT in its own translation unit.
 #define RAPRO_DETECT_DEFINE_KT(KTV)                                                                    \
@@ -595,35 +725,42 @@ template <> cudaError_t detect_prepare_kt<16>(int smem);
     dim3 grid((L.P.N + DET_SC - 1) / DET_SC, L.P.T);                                                   \
     dim3 block(det_block_threads(L.P.tiles));                                                          \
     const int v = (L.P.D > 6 ? 1 : 0) + (L.tma ? 2 : 0) + (L.P.fix_count ? 4 : 0);                    \
+    if (L.fused) {                                                                                     \
+      if (L.P.D > 6) RAPRO_DETECT_GO(KTV, 12, true, DET_FUSED);                                        \
+      else RAPRO_DETECT_GO(KTV, 6, true, DET_FUSED);                                                   \
+      return cudaGetLastError();                                                                       \
+    }                                                                                                  \
     switch (v) {                                                                                       \
-      case 0: RAPRO_DETECT_GO(KTV, 6, false, false); break;                                            \
-      case 1: RAPRO_DETECT_GO(KTV, 12, false, false); break;                                           \
-      case 2: RAPRO_DETECT_GO(KTV, 6, true, false); break;                                             \
-      case 3: RAPRO_DETECT_GO(KTV, 12, true, false); break;                                            \
-      case 4: RAPRO_DETECT_GO(KTV, 6, false, true); break;                                             \
-      case 5: RAPRO_DETECT_GO(KTV, 12, false, true); break;                                            \
-      case 6: RAPRO_DETECT_GO(KTV, 6, true, true); break;                                              \
-      default: RAPRO_DETECT_GO(KTV, 12, true, true); break;                                            \
+      case 0: RAPRO_DETECT_GO(KTV, 6, false, DET_PLAIN); break;                                        \
+      case 1: RAPRO_DETECT_GO(KTV, 12, false, DET_PLAIN); break;                                       \
+      case 2: RAPRO_DETECT_GO(KTV, 6, true, DET_PLAIN); break;                                         \
+      case 3: RAPRO_DETECT_GO(KTV, 12, true, DET_PLAIN); break;                                        \
+      case 4: RAPRO_DETECT_GO(KTV, 6, false, DET_FIX); break;                                          \
+      case 5: RAPRO_DETECT_GO(KTV, 12, false, DET_FIX); break;                                         \
+      case 6: RAPRO_DETECT_GO(KTV, 6, true, DET_FIX); break;                                           \
+      default: RAPRO_DETECT_GO(KTV, 12, true, DET_FIX); break;                                         \
     }                                                                                                  \
     return cudaGetLastError();                                                                         \
   }                                                                                                    \
   template <>                                                                                          \
-  cudaError_t detect_prepare_kt<KTV>(int smem) {                                                       \
+  cudaError_t detect_prepare_kt<KTV>(int smem, int fused_smem) {                                       \
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;                           \
-    cudaError_t e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true, false>, A, smem);                 \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true, false>, A, smem);      \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, false, false>, A, smem);      \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, false, false>, A, smem);     \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true, true>, A, smem);        \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true, true>, A, smem);       \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, false, true>, A, smem);       \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, false, true>, A, smem);      \
+    cudaError_t e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true, DET_PLAIN>, A, smem);             \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true, DET_PLAIN>, A, smem);  \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, false, DET_PLAIN>, A, smem);  \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, false, DET_PLAIN>, A, smem); \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true, DET_FIX>, A, smem);     \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true, DET_FIX>, A, smem);    \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, false, DET_FIX>, A, smem);    \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, false, DET_FIX>, A, smem);   \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 6, true, DET_FUSED>, A, fused_smem);  \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(detect_kernel<KTV, 12, true, DET_FUSED>, A, fused_smem); \
     return e;                                                                                          \
   }
 
-#define RAPRO_DETECT_GO(KTV, DTV, TMA, FIXV)                                                            \
-  detect_kernel<KTV, DTV, TMA, FIXV><<<grid, block, L.smem, L.stream>>>(L.map_h, L.map_y, L.h, L.y,    \
-                                                                        L.x_eq, L.labels, L.llr,       \
-                                                                        L.info, L.P)
+#define RAPRO_DETECT_GO(KTV, DTV, TMA, MODEV)                                                           \
+  detect_kernel<KTV, DTV, TMA, MODEV><<<grid, block, L.smem, L.stream>>>(L.map_h, L.map_y, L.h, L.y,   \
+                                                                         L.x_eq, L.labels, L.llr,      \
+                                                                         L.info, L.P)
 
 }  // namespace rapro

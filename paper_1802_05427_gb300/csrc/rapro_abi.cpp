@@ -66,6 +66,10 @@ rapro_status receive_on(const Plan* pl, const rapro_c32* y_pilot, const rapro_c3
     return bad("y_pilot, pilots, y_data and x_eq must not be NULL");
   rapro_status s = check_device(pl);
   if (s != RAPRO_OK) return s;
+  if (pl->recv_form == RAPRO_RECV_FUSED && receive_fused_ok(*pl, y_pilot, y_data))
+    return launched(launch_receive_fused(*pl, f2(y_pilot), f2(pilots), f2(y_data), h_out ? f2(h_out) : nullptr,
+                                         f2(x_eq), labels, llr, info, st),
+                    "fused receive kernel launch");
   float2* h = h_out ? f2(h_out) : pl->d_h_work;
   if ((s = bf16_check(pl, y_pilot, pilots, h, nullptr)) != RAPRO_OK) return s;
   cudaError_t e = pl->comb ? launch_comb(*pl, f2(y_pilot), f2(pilots), h, st)

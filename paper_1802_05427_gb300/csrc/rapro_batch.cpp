@@ -124,6 +124,52 @@ rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const r
     }
   }
   pl->tiles.msplit = best_split;
+  pl->recv_form = RAPRO_RECV_SPLIT;
+  // The fused receive form against the tuned two-kernel form, where it applies.
+  if (receive_fused_ok(*pl, y_pilot, y_data)) {
+    const float split_ms = time_on(st, kWarm, kReps, [&] {
+      cudaError_t r = launch_lmmse(*pl, y, pil, pl->d_w_main, pl->d_w_tail, nullptr, nullptr, hh, st);
+      return r != cudaSuccess ? r : launch_detect(*pl, hh, yd, xx, nullptr, nullptr, nullptr, st);
+    });
+    if (split_ms < 0.f) return cuda_fail(cudaGetLastError(), "two-kernel receive during tuning");
+    int best_fused = -1;
+    float fused_ms = 0.f;
+    for (int split = 1; split <= dflt; ++split) {
+      pl->tiles.msplit = split;
+      const float ms = time_on(st, kWarm, kReps, [&] {
+        return launch_receive_fused(*pl, y, pil, yd, nullptr, xx, nullptr, nullptr, nullptr, st);
+      });
+      if (ms < 0.f) {
+        pl->tiles.msplit = best_split;
+        return cuda_fail(cudaGetLastError(), "fused receive during tuning");
+      }
+      if (best_fused < 0 || ms < fused_ms) {
+        best_fused = split;
+        fused_ms = ms;
+      }
+    }
+    if (fused_ms < split_ms) {
+      pl->recv_form = RAPRO_RECV_FUSED;
+      pl->tiles.msplit = best_fused;
+    } else {
+      pl->tiles.msplit = best_split;
+    }
+  }
+  return RAPRO_OK;
+}
+
+rapro_status rapro_plan_set_receive_form(rapro_plan* plan, int form) {
+  if (!plan) return bad("plan is NULL");
+  if (form != RAPRO_RECV_FUSED && form != RAPRO_RECV_SPLIT) return bad("form must be a rapro_receive_form");
+  reinterpret_cast<Plan*>(plan)->recv_form = form;
+  return RAPRO_OK;
+}
+
+rapro_status rapro_receive_is_fused(const rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* y_data,
+                                    int* fused) {
+  if (!plan || !fused) return bad("plan and fused must not be NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  *fused = pl->recv_form == RAPRO_RECV_FUSED && receive_fused_ok(*pl, y_pilot, y_data) ? 1 : 0;
   return RAPRO_OK;
 }
 

@@ -49,6 +49,7 @@ struct Plan {
   int* d_status = nullptr;         // device status word
   void* d_w_tc = nullptr;          // tensor-core filter operand (canonical layout), or null
   int est_variant = -1;            // estimator kernel (EST_*), -1 = built-in choice; set by rapro_plan_tune
+  int recv_form = RAPRO_RECV_SPLIT; // rapro_receive_form of rapro_receive_subframe
   int* d_fix = nullptr;            // precision form: FP64-fallback count, ticket, list [T n_sc]
   bool comb = false;               // comb pilot layout (Sec. II)
   std::vector<float2> w_comb;      // comb weights [sets][Q][Q][Q] (3W: 1 set, S-W: K sets)
@@ -115,6 +116,13 @@ cudaError_t launch_lmmse_tc(const Plan& pl, const float2* y, const float2* pil, 
 
 cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
                           unsigned char* labels, float* llr, int* info, cudaStream_t st);
+
+// Fused receive form: LS, LMMSE and detection in one kernel (orthogonal FP32 plans, even
+// B <= 16, 16-byte aligned y_pilot and y_data); h_out may be null.
+bool receive_fused_ok(const Plan& pl, const void* y_pilot, const void* y_data);
+cudaError_t launch_receive_fused(const Plan& pl, const float2* y_pilot, const float2* pil, const float2* y_data,
+                                 float2* h_out, float2* x_eq, unsigned char* labels, float* llr, int* info,
+                                 cudaStream_t st);
 
 // Plan-free launchers used by the allocation-free receive entry point.
 cudaError_t launch_ls_lmmse_small_raw(const float2* w_main, const float2* w_tail, int B, int tail,

@@ -23,6 +23,7 @@ RAPRO_PILOT_ORTHOGONAL, RAPRO_PILOT_COMB = 0, 1
 RAPRO_PDP_EXP, RAPRO_PDP_UNIFORM_L = 0, 1
 RAPRO_COMB_3W, RAPRO_COMB_SW, RAPRO_COMB_INTERP3 = 0, 1, 2
 RAPRO_PREC_FP32, RAPRO_PREC_BF16 = 0, 1
+RAPRO_RECV_SPLIT, RAPRO_RECV_FUSED = 0, 1
 RAPRO_MAX_PILOT_SYM = 8
 
 
@@ -72,6 +73,8 @@ def lib() -> ctypes.CDLL:
         "rapro_mse_backward": ([_P] * 12, ctypes.c_int),
         "rapro_plan_tune": ([_P] * 7, ctypes.c_int),
         "rapro_plan_variant": ([_P, _P, _P], ctypes.c_int),
+        "rapro_plan_set_receive_form": ([_P, ctypes.c_int], ctypes.c_int),
+        "rapro_receive_is_fused": ([_P, _P, _P, _P], ctypes.c_int),
         "rapro_batch_create": ([ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
         "rapro_batch_destroy": ([_P], ctypes.c_int),
         "rapro_receive_batch": ([_P, ctypes.POINTER(RaproJob), ctypes.c_int, _P], ctypes.c_int),
@@ -297,6 +300,22 @@ def rapro_plan_variant(plan: Plan):
     ev, ds = ctypes.c_int(), ctypes.c_int()
     _check(lib().rapro_plan_variant(plan.handle, ctypes.byref(ev), ctypes.byref(ds)), "rapro_plan_variant")
     return ev.value, ds.value
+
+
+def rapro_plan_set_receive_form(plan: Plan, form: int) -> None:
+    _check(lib().rapro_plan_set_receive_form(plan.handle, int(form)), "rapro_plan_set_receive_form")
+
+
+def rapro_receive_is_fused(plan: Plan, y_pilot, y_data) -> bool:
+    """Whether rapro_receive_subframe with these tensors runs the fused kernel."""
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    f = ctypes.c_int()
+    _check(lib().rapro_receive_is_fused(plan.handle, _ptr(y_pilot, s["y_pilot"], c64, "y_pilot"),
+                                        _ptr(y_data, s["y_data"], c64, "y_data"), ctypes.byref(f)),
+           "rapro_receive_is_fused")
+    return bool(f.value)
 
 
 class Batch:

@@ -296,6 +296,112 @@ def test_receive_without_h_out_and_uniform_L_model():
     check_detection(g, o, sh.qam_bits)
 
 
+# ------------------------------------------ fused receive form (one kernel per subframe)
+FUSED_CASES = [
+    # name, shape, B: block sizes that give pilot boxes of 12 .. 30 subcarriers, tail blocks,
+    # n_sc not a multiple of the 16-subcarrier tile, antennas not a multiple of the 8-antenna
+    # chunk, 1..16 users (16: several users per half-warp), 12 data symbols per slot
+    ("tiny_B12", synth.TINY, 12),
+    ("B2", synth.SubframeShape(M=9, K=3, n_sc=50, n_fft=128, qam_bits=2), 2),
+    ("B4_K1", synth.SubframeShape(M=16, K=1, n_sc=36, n_fft=64, qam_bits=4), 4),
+    ("B6_tail", synth.SubframeShape(M=20, K=5, n_sc=100, n_fft=256, snr_db=12.0, qam_bits=4), 6),
+    ("B8", synth.SubframeShape(M=24, K=8, n_sc=120, n_fft=256, qam_bits=6), 8),
+    ("B10_tail", synth.SubframeShape(M=13, K=6, n_sc=104, n_fft=256, qam_bits=4), 10),
+    ("B12_tail_K16", synth.SubframeShape(M=40, K=16, n_sc=206, n_fft=512, n_taps=8, tau_rms=5.0,
+                                         snr_db=20.0, qam_bits=4), 12),
+    ("B14_D12", synth.SubframeShape(M=17, K=12, n_sc=140, n_fft=256, qam_bits=2, n_data_per_slot=12), 14),
+    ("B16_K16_D12", synth.SubframeShape(M=32, K=16, n_sc=96, n_fft=128, qam_bits=6, n_data_per_slot=12,
+                                        snr_db=25.0), 16),
+]
+
+
+@pytest.mark.parametrize("name,sh,B", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
+def test_fused_receive_matches_the_oracle(name, sh, B):
+    """Eq. 9, 12, 20-22 in one kernel: h (when asked for), x~, labels, LLRs and info as
+    the oracle; without h_out the same outputs and nothing else written."""
+    sf, c64 = _inputs(sh, synth.SEED_BASE + 40)
+    o = oracle_receive(sh, c64, B)
+    plan = R.Plan(params_for(sh, B))
+    s = plan.shapes()
+    yp, pil, yd = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"])
+    assert not R.rapro_receive_is_fused(plan, yp, yd)            # the default form is split
+    R.rapro_plan_set_receive_form(plan, R.RAPRO_RECV_FUSED)
+    assert R.rapro_receive_is_fused(plan, yp, yd)
+    for with_h in (True, False):
+        x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+        lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
+        llr = torch.empty(s["llr"], dtype=torch.float32, device="cuda")
+        info = torch.full(s["info"], -7, dtype=torch.int32, device="cuda")
+        h = torch.full(s["h"], 3.0 + 1j, dtype=torch.complex64, device="cuda") if with_h else None
+        R.rapro_receive_subframe(plan, yp, pil, yd, x, lab, llr, info, h_out=h)
+        g = dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr), info=_host(info))
+        if with_h:
+            assert rel_err_per(_host(h), o["h"], axes=(2, 3)).max() <= TOL
+        check_detection(g, o, sh.qam_bits)
+        assert np.all(g["info"] == 0)
+    assert plan.device_status() == 0
+    plan.close()
+
+
+def test_fused_and_split_forms_agree_and_the_form_is_selectable():
+    sh = synth.SubframeShape(M=32, K=12, n_sc=192, n_fft=256, snr_db=15.0, qam_bits=4)
+    sf, c64 = _inputs(sh, synth.SEED_BASE + 41)
+    o = oracle_receive(sh, c64, 12)
+    plan = R.Plan(params_for(sh, 12))
+    s = plan.shapes()
+    yp, pil, yd = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"])
+    outs = {}
+    for form in (R.RAPRO_RECV_SPLIT, R.RAPRO_RECV_FUSED):
+        R.rapro_plan_set_receive_form(plan, form)
+        assert R.rapro_receive_is_fused(plan, yp, yd) == (form == R.RAPRO_RECV_FUSED)
+        x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+        lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
+        R.rapro_receive_subframe(plan, yp, pil, yd, x, lab)
+        outs[form] = (_host(x), _host(lab))
+        e = rel_err_per(outs[form][0], o["x_eq"], axes=(2,))
+        assert e.max() <= TOL
+    # both forms round differently (LS folded into the weights), but only in the last bits
+    assert rel_err_per(outs[0][0], outs[1][0], axes=(2,)).max() <= 2 * TOL
+    with pytest.raises(R.RaproError):
+        R.rapro_plan_set_receive_form(plan, 7)
+    plan.close()
+
+
+def test_fused_form_applies_only_where_its_rules_hold():
+    """Odd n_sc, B > 16, odd B, BF16 plans, comb plans and unaligned arrays take the
+    two-kernel form (and still match the oracle where it is run here)."""
+    sh = synth.SubframeShape(M=16, K=4, n_sc=96, n_fft=128, qam_bits=2)
+    sf, c64 = _inputs(sh, synth.SEED_BASE + 42)
+    yp, yd = _dev(c64["y_pilot"]), _dev(c64["y_data"])
+    def fused_plan(p):
+        plan = R.Plan(p)
+        R.rapro_plan_set_receive_form(plan, R.RAPRO_RECV_FUSED)
+        return plan
+
+    for B, ok in ((12, True), (48, False), (9, False), (16, True)):
+        with fused_plan(params_for(sh, B)) as plan:
+            assert R.rapro_receive_is_fused(plan, yp, yd) == ok, B
+    p = params_for(sh, 12)
+    p.precision = R.RAPRO_PREC_BF16
+    with fused_plan(p) as plan:
+        assert not R.rapro_receive_is_fused(plan, yp, yd)
+    sh_odd = synth.SubframeShape(M=8, K=2, n_sc=75, n_fft=128, qam_bits=2)
+    sfo, co = _inputs(sh_odd, 3)
+    with fused_plan(params_for(sh_odd, 10)) as plan:
+        assert not R.rapro_receive_is_fused(plan, _dev(co["y_pilot"]), _dev(co["y_data"]))
+    # an 8-byte offset view: same values, not 16-byte aligned
+    with fused_plan(params_for(sh, 12)) as plan:
+        s = plan.shapes()
+        buf = torch.empty(int(np.prod(s["y_pilot"])) + 1, dtype=torch.complex64, device="cuda")
+        ypu = buf[1:].view(s["y_pilot"])
+        ypu.copy_(yp)
+        assert not R.rapro_receive_is_fused(plan, ypu, yd)
+        x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+        R.rapro_receive_subframe(plan, ypu, _dev(c64["pilots"]), yd, x)
+        o = oracle_receive(sh, c64, 12)
+        assert rel_err_per(_host(x), o["x_eq"], axes=(2,)).max() <= TOL
+
+
 def test_invalid_pointers_are_rejected_without_launch():
     sh = synth.TINY
     plan = R.Plan(params_for(sh, 12))
@@ -641,6 +747,8 @@ def test_autotuner_picks_an_applicable_kernel_and_keeps_parity(case):
     assert ev in (0, 1, 2, 3) and split in (1, 2)
     if B > 32:
         assert ev == 3
+    if B > 16:
+        assert not R.rapro_receive_is_fused(plan, yp, yd)   # the fused form does not apply
     lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
     llr = torch.empty(s["llr"], dtype=torch.float32, device="cuda")
     R.rapro_receive_subframe(plan, yp, pil, yd, x, lab, llr, h_out=h)
