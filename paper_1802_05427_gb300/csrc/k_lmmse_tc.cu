@@ -46,33 +46,12 @@ constexpr int TC_STAGES = 4;        // raw-tile ring depth
 constexpr int TC_CONSUMERS = 256;    // two threads per row-block, one per half of its reals
 constexpr int TC_THREADS = TC_CONSUMERS + 64;   // + one MMA warp + one copy warp
 
-// High part of the split x = hi + lo: x truncated to TF32 (10 explicit mantissa bits), so
-// that lo = x - hi is exact in FP32; the MMA reads lo at TF32 precision, an error of at
-// most 2^-20 |x|.
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
-
-// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 bytes,
-// lbo = byte distance between cores adjacent along K, sbo = between 8-row groups.
-__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
-  return uint64_t((smem_u32(p) >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
-         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
-}
-
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = TC_N.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(TC_N >> 3) << 17) |
-                                (uint32_t(TC_ROWS >> 4) << 24);
+// The TF32 passes use the shared M = 128, N = 32 instruction (rapro_ptx.cuh).
+static_assert(TC_ROWS == 128 && TC_N == 32, "the TF32 MMA helper is M = 128, N = 32");
 
 // Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = TC_N.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TC_N >> 3) << 17) |
                                 (uint32_t(TC_ROWS >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdescTf32), "r"(accumulate ? 1 : 0)
-      : "memory");
-}
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
   asm volatile(
@@ -85,19 +64,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (lower address) = lo
   return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 }  // namespace
@@ -231,15 +197,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* _
         const uint32_t d = tmem + uint32_t(buf * TC_N);
 #pragma unroll
         for (int kg = 0; kg < KSTEPS; ++kg) {
-          const uint64_t dah = smem_desc(ah + kg * 256, 128, SBO), dbh = smem_desc(sBh + kg * 256, 128, SBO);
+          const uint64_t dah = smem_desc_kmajor(ah + kg * 256, 128, SBO), dbh = smem_desc_kmajor(sBh + kg * 256, 128, SBO);
           if (BF) {
             mma_bf16(d, dah, dbh, kg > 0);
           } else {
-            const uint64_t dal = smem_desc(al + kg * 256, 128, SBO);
-            const uint64_t dbl = smem_desc(sBh + B_BYTES + kg * 256, 128, SBO);
-            mma_tf32(d, dah, dbh, kg > 0);
-            mma_tf32(d, dah, dbl, true);
-            mma_tf32(d, dal, dbh, true);
+            const uint64_t dal = smem_desc_kmajor(al + kg * 256, 128, SBO);
+            const uint64_t dbl = smem_desc_kmajor(sBh + B_BYTES + kg * 256, 128, SBO);
+            mma_tf32_m128n32(d, dah, dbh, kg > 0);
+            mma_tf32_m128n32(d, dah, dbl, true);
+            mma_tf32_m128n32(d, dal, dbh, true);
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -300,7 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* _
 #pragma unroll
         for (int j = 0; j < KH; ++j) {
           const int kg = half * KH + j;
-          const float4 h = make_float4(tf32_hi(q[j].x), tf32_hi(q[j].y), tf32_hi(q[j].z), tf32_hi(q[j].w));
+          const float4 h = make_float4(tf32_trunc(q[j].x), tf32_trunc(q[j].y), tf32_trunc(q[j].z), tf32_trunc(q[j].w));
           const float4 l = make_float4(q[j].x - h.x, q[j].y - h.y, q[j].z - h.z, q[j].w - h.w);
           const int off = (r / 8) * SBO + kg * 128 + (r % 8) * 16;
           *reinterpret_cast<float4*>(ah + off) = h;

@@ -99,6 +99,46 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// ------------------------------------------------------------ tcgen05 (TF32 operands)
+// High part of the split x = hi + lo: x truncated to TF32 (10 explicit mantissa bits), so
+// that lo = x - hi is exact in FP32; an MMA reads lo at TF32 precision, an error of at most
+// 2^-20 |x|.
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 bytes,
+// lbo = byte distance between cores adjacent along K, sbo = between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc_kmajor(const void* p, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((smem_u32(p) >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 32.
+constexpr uint32_t kIdescTf32M128N32 = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(32 >> 3) << 17) |
+                                       (uint32_t(128 >> 4) << 24);
+
+// D[tmem] (+)= A B^T for one K step of 8 TF32 values, issued by one thread.
+__device__ __forceinline__ void mma_tf32_m128n32(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescTf32M128N32), "r"(accumulate ? 1 : 0)
+      : "memory");
+}
+
+// 32 consecutive columns of this warp's 32 TMEM lanes (thread i: lane base + i), waited for.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Complex helpers on float2 = {re, im}.
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));

@@ -362,6 +362,7 @@ def test_fused_and_split_forms_agree_and_the_form_is_selectable():
         assert e.max() <= TOL
     # both forms round differently (LS folded into the weights), but only in the last bits
     assert rel_err_per(outs[0][0], outs[1][0], axes=(2,)).max() <= 2 * TOL
+    assert (outs[0][1] == outs[1][1]).mean() > 0.999
     with pytest.raises(R.RaproError):
         R.rapro_plan_set_receive_form(plan, 7)
     plan.close()
