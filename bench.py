@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "uplink REs detected/s at 128x12, 1200 sc (FP32 vs BF16-TC); % roofline"
 UNIT = "REs/s"
 N_SETS = 8                   # resident input subframes rotated through (> L2 in total)
-GRAPH_STEPS = N_SETS         # steps per captured CUDA graph
-IN_FLIGHT = 2                # subframes in flight: consecutive steps alternate between 2 streams
+GRAPH_STEPS = 3 * N_SETS     # steps per captured CUDA graph
+IN_FLIGHT = 4                # subframes in flight: consecutive steps rotate over 4 streams
 L2_BYTES = 129 * 2 ** 20
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 
@@ -79,7 +79,11 @@ def algorithmic(sh, B):
     res = T * D * N
     det_bytes = c * n_h + c * T * D * M * N + c * T * D * K * N + T * D * K * N + 4 * T * N
     det_flops = (T * N * (8 * M * K * (K + 1) // 2 + 8 * K ** 3 // 6)) + res * (8 * M * K + 8 * K * K)
-    return dict(ls_lmmse=est, detect=dict(bytes=det_bytes, flops=det_flops), res_per_step=res)
+    # the whole path as one algorithm (Eq. 9, 12, 20-22): inputs once, results once, h on chip
+    path_bytes = (c * n_h + c * T * K * N + c * T * D * M * N + w_bytes + c * T * D * K * N + T * D * K * N
+                  + 4 * T * N)
+    path = dict(bytes=path_bytes, flops=est["flops"] + det_flops)
+    return dict(ls_lmmse=est, detect=dict(bytes=det_bytes, flops=det_flops), path=path, res_per_step=res)
 
 
 def peaks():
@@ -183,7 +187,7 @@ def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3):
     ms8t = timed(8)
     counts = {}
     for j in jobs:
-        ev, _ = R.rapro_plan_variant(j["plan"])
+        ev = R.rapro_plan_variant(j["plan"])[0]
         counts[str(ev)] = counts.get(str(ev), 0) + 1
     for j in jobs:
         assert j["plan"].device_status() == 0
@@ -544,19 +548,29 @@ def run_rapro(args):
             ps = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=Bs, sigma2=sh.sigma2,
                                qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms)
             with R.Plan(ps) as pl2:
-                def step2(i):
-                    d = sets[i % N_SETS]
-                    R.rapro_ce_ls_lmmse(pl2, d["y_pilot"], d["pilots"], h)
-                    R.rapro_mmse_detect(pl2, h, d["y_data"], x, lab, None, info)
+                def step2(i, stream=None):
+                    d, o = sets[i % N_SETS], outs[i % IN_FLIGHT]
+                    R.rapro_ce_ls_lmmse(pl2, d["y_pilot"], d["pilots"], o["h"], stream=stream)
+                    R.rapro_mmse_detect(pl2, o["h"], d["y_data"], o["x"], o["lab"], None, o["info"], stream=stream)
                 for i in range(3):
                     step2(i)
+                # the same pipelining as the headline: consecutive steps rotate over IN_FLIGHT streams
                 g = torch.cuda.CUDAGraph()
                 st = torch.cuda.Stream()
+                side = [torch.cuda.Stream() for _ in range(IN_FLIGHT)]
                 st.wait_stream(torch.cuda.current_stream())
                 with torch.cuda.stream(st):
                     with torch.cuda.graph(g, stream=st):
+                        fork = torch.cuda.Event()
+                        fork.record(st)
+                        for q in side:
+                            q.wait_event(fork)
                         for i in range(GRAPH_STEPS):
-                            step2(i)
+                            step2(i, stream=side[i % IN_FLIGHT])
+                        for q in side:
+                            join = torch.cuda.Event()
+                            join.record(q)
+                            st.wait_event(join)
                 torch.cuda.synchronize()
                 r2 = 64 if Bs < 1200 else 4
                 e0.record()
@@ -737,6 +751,16 @@ def run_rapro(args):
             "frac": r["frac"], "traffic": traffic, "kernel": dom,
             "peak_source": (f"{peak_kind} HBM copy bandwidth" if r["bound"] == "hbm" else
                             "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)")}
+    # the path against its own roofline: t_roof = max(bytes / HBM, flops / FP32 FMA peak)
+    pa = alg["path"]
+    t_step = ms / args.steps * 1e-3
+    t_roof = max(pa["bytes"] / (hbm * 1e9), pa["flops"] / (ALU_PEAK_TFLOPS * 1e12))
+    path_roof = {"bound": "hbm" if pa["bytes"] / (hbm * 1e9) >= pa["flops"] / (ALU_PEAK_TFLOPS * 1e12) else "alu",
+                 "alg_bytes": pa["bytes"], "alg_flops": pa["flops"], "t_roof_us": t_roof * 1e6,
+                 "t_step_us": t_step * 1e6, "frac": t_roof / t_step,
+                 "note": "whole step (estimator + detector, subframes in flight) against max(algorithmic "
+                         "bytes / HBM peak, algorithmic flops / FP32 FMA peak)"}
+    ev, dsplit, egrid = R.rapro_plan_variant(plan)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -745,8 +769,9 @@ def run_rapro(args):
                        "res_per_step": res_per_step, "parallelism": f"replicas x{world}",
                        "l2": f"{N_SETS} resident input subframes rotated ({N_SETS * in_bytes / 2**20:.0f} MiB > "
                              f"{L2_BYTES / 2**20:.0f} MiB L2)",
-                       "launch": f"CUDA graph replays of {GRAPH_STEPS} steps; consecutive steps alternate "
-                                 f"between {IN_FLIGHT} streams, so {IN_FLIGHT} subframes are in flight"},
+                       "launch": f"CUDA graph replays of {GRAPH_STEPS} steps; consecutive steps rotate "
+                                 f"over {IN_FLIGHT} streams, so {IN_FLIGHT} subframes are in flight",
+                       "plan_variant": {"est_variant": ev, "det_split": dsplit, "est_ctas_per_sm": egrid}},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": whole_job_value(world, res_per_step, args.e2e_steps, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -754,7 +779,10 @@ def run_rapro(args):
                            "so one subframe's copies overlap the previous one's kernels)",
                     "host_link_gbs": h2d * args.e2e_steps / (e2e_ms * 1e-3) / 1e9},
             "gpu_launches": 2 * args.steps, "clocks": clk,
-            "kernels": rows, "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K,
+            "path_roofline": path_roof,
+            "kernels": rows, "kernel_timing": f"graphs of {GRAPH_STEPS} launches of one kernel alone on one "
+                                              "stream, same plan variant as the timed step",
+            "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K,
             "comb_pilots": comb, "precision_form": prec, "differentiable": diff,
             "batched_heterogeneous": hetero}
     print(json.dumps(line), flush=True)

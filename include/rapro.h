@@ -282,21 +282,31 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
 
 /*
  * Autotuner (no counterpart in the paper, whose receiver has one code path): times every
- * estimator kernel that applies to the plan's shape and these arrays (tensor cores,
- * streaming, row-segment and tiled kernels; comb plans have one) and the detector's
- * warps-per-role split, then (where it applies to these arrays) the fused receive form with
- * each split against the tuned two-kernel form, 2 warm and 5 timed launches each on the
- * caller's stream, and keeps the fastest in the plan: estimator, split and receive form
- * (later calls with arrays a choice does not apply to fall back to the built-in choice).
- * Overwrites h and x_eq.  Synchronises the stream; not inside a
+ * combination of the estimator kernels that apply to the plan's shape and these arrays
+ * (tensor cores with one or as many CTAs per SM as fit, streaming, row-segment and tiled
+ * kernels; comb plans have one), the detector's warps per role and (where it applies) the
+ * fused receive form, each as whole receives with four subframes in flight on streams of
+ * the library's (one at a time for RAPRO_PREC_BF16 plans), 2 warm and 5 timed rounds, and
+ * keeps the one with the best throughput in the plan (later calls with arrays a choice does
+ * not apply to fall back to the built-in choice).  Overwrites h and x_eq.  Synchronises the stream; not inside a
  * stream capture.  The plan must not be in use by another stream meanwhile.
  */
 rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const rapro_c32* pilots,
                              const rapro_c32* y_data, rapro_c32* h, rapro_c32* x_eq, rapro_stream stream);
 
 /* The plan's kernel choices: estimator kernel (-1 built-in, 0 tensor cores, 1 streaming,
- * 2 row segments, 3 tiled) and the detector's warps per role.  Either pointer may be NULL. */
-rapro_status rapro_plan_variant(const rapro_plan* plan, int* est_variant, int* det_split);
+ * 2 row segments, 3 tiled), the detector's warps per role, and the tensor-core estimator's
+ * CTAs per SM (0: as many as fit).  A new plan has -1, 1 and 1: one warp per role and one
+ * estimator CTA per SM leave room on every SM for an estimator and a detector CTA of two
+ * subframes in flight.  Any pointer may be NULL. */
+rapro_status rapro_plan_variant(const rapro_plan* plan, int* est_variant, int* det_split, int* est_ctas_per_sm);
+
+/* Set the plan's kernel choices by hand (as rapro_plan_tune would): est_variant -1 (built-in)
+ * or 0..3 as above (a choice that does not apply to later calls' arrays falls back to the
+ * built-in one), det_split 1 or 2 (at most 2 when the detector has at most 8 roles, else 1),
+ * est_ctas_per_sm 0..8.  RAPRO_ERR_INVALID_ARG otherwise.  Not while another stream uses the
+ * plan. */
+rapro_status rapro_plan_set_variant(rapro_plan* plan, int est_variant, int det_split, int est_ctas_per_sm);
 
 /* Set the plan's receive form (rapro_receive_form; RAPRO_ERR_INVALID_ARG otherwise).  Not
  * while another stream uses the plan. */

@@ -378,6 +378,7 @@ static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil,
   const int regs_warp = ((std::max(fa.numRegs, 1) + 7) / 8 * 8) * 32;
   int per_sm = int(size_t(smem_sm) / (smem + size_t(reserved)));
   per_sm = std::max(1, std::min({per_sm, 2048 / TC_THREADS, 512 / (2 * TC_N), 65536 / (regs_warp * (TC_THREADS / 32))}));
+  if (pl.est_ctas_per_sm > 0) per_sm = std::min(per_sm, pl.est_ctas_per_sm);
   const int grid = std::min(n_tiles, per_sm * sms);
   lmmse_tc_kernel<KR, BF><<<grid, TC_THREADS, smem, st>>>(y, pil, out, M, N, B, n_rb, n_tiles, pl.d_status,
                                                             pl.d_w_tc);

@@ -87,74 +87,114 @@ rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const r
   const float2* yd = reinterpret_cast<const float2*>(y_data);
   float2* hh = reinterpret_cast<float2*>(h);
   float2* xx = reinterpret_cast<float2*>(x_eq);
-  constexpr int kWarm = 2, kReps = 5;
-  if (!pl->comb) {
-    int best = -1;
-    float best_ms = 0.f;
-    for (int v = 0; v < EST_VARIANTS; ++v) {
-      if (!lmmse_variant_ok(*pl, v, y, pil, hh)) continue;
-      const float ms = time_on(st, kWarm, kReps, [&] { return launch_lmmse_variant(*pl, v, y, pil, hh, st); });
-      if (ms < 0.f) return cuda_fail(cudaGetLastError(), "estimator variant during tuning");
-      if (best < 0 || ms < best_ms) {
-        best = v;
-        best_ms = ms;
+  // Candidates run as whole receives with kInFlight copies in flight on streams of their own
+  // (the same inputs and outputs: every copy writes the same values), so that the choice
+  // is the one with the best throughput of pipelined subframes.  A BF16 plan's detectors
+  // share the FP64-fallback list, so its copies run one at a time.
+  constexpr int kWarm = 2, kReps = 5, kInFlight = 4;
+  const int in_flight = pl->d_fix ? 1 : kInFlight;
+  cudaStream_t side[kInFlight] = {};
+  cudaEvent_t fork = nullptr, join[kInFlight] = {};
+  auto cleanup = [&] {
+    for (int i = 0; i < kInFlight; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  };
+  e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int i = 0; i < kInFlight && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "tuning streams");
+  }
+  // One round: every side stream runs `fn` once, forked from and joined into st.
+  auto round = [&](auto fn) -> cudaError_t {
+    cudaError_t r = cudaEventRecord(fork, st);
+    for (int i = 0; i < in_flight && r == cudaSuccess; ++i) {
+      r = cudaStreamWaitEvent(side[i], fork, 0);
+      if (r == cudaSuccess) r = fn(side[i]);
+      if (r == cudaSuccess) r = cudaEventRecord(join[i], side[i]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(st, join[i], 0);
+    }
+    return r;
+  };
+  auto receive_split = [&](cudaStream_t q) {
+    cudaError_t r = pl->comb ? launch_comb(*pl, y, pil, hh, q)
+                             : launch_lmmse(*pl, y, pil, pl->d_w_main, pl->d_w_tail, nullptr, nullptr, hh, q);
+    return r != cudaSuccess ? r : launch_detect(*pl, hh, yd, xx, nullptr, nullptr, nullptr, q);
+  };
+  const int max_split = make_det_tiles(pl->p.K, pl->D).msplit;
+  float best_ms = -1.f;
+  int best_v = pl->est_variant, best_g = pl->est_ctas_per_sm, best_split = pl->tiles.msplit, best_form = RAPRO_RECV_SPLIT;
+  auto consider = [&](int v, int g, int split, int form, float ms) {
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best_v = v;
+      best_g = g;
+      best_split = split;
+      best_form = form;
+    }
+  };
+  rapro_status status = RAPRO_OK;
+  for (int v = pl->comb ? -1 : 0; v < (pl->comb ? 0 : EST_VARIANTS) && status == RAPRO_OK; ++v) {
+    if (v >= 0 && !lmmse_variant_ok(*pl, v, y, pil, hh)) continue;
+    for (int g : {1, 0}) {
+      if (g == 0 && v != EST_TC) continue;        // the grid choice concerns the tensor-core kernel
+      for (int split = 1; split <= max_split; ++split) {
+        pl->est_variant = v;
+        pl->est_ctas_per_sm = g;
+        pl->tiles.msplit = split;
+        const float ms = time_on(st, kWarm, kReps, [&] { return round(receive_split); });
+        if (ms < 0.f) {
+          status = cuda_fail(cudaGetLastError(), "receive candidate during tuning");
+          break;
+        }
+        consider(v, g, split, RAPRO_RECV_SPLIT, ms);
       }
     }
-    pl->est_variant = best;
   }
-  // the detector reads the estimate just written
-  e = pl->comb ? launch_comb(*pl, y, pil, hh, st) : launch_lmmse(*pl, y, pil, pl->d_w_main, pl->d_w_tail,
-                                                                  nullptr, nullptr, hh, st);
-  if (e != cudaSuccess) return cuda_fail(e, "estimator during tuning");
-  const int dflt = make_det_tiles(pl->p.K, pl->D).msplit;
-  int best_split = dflt;
-  float best_ms = -1.f;
-  for (int split = 1; split <= dflt; ++split) {
+  pl->recv_form = RAPRO_RECV_FUSED;
+  const bool mode_fused = status == RAPRO_OK && receive_fused_ok(*pl, y_pilot, y_data);
+  for (int split = 1; split <= max_split && mode_fused; ++split) {
     pl->tiles.msplit = split;
     const float ms = time_on(st, kWarm, kReps, [&] {
-      return launch_detect(*pl, hh, yd, xx, nullptr, nullptr, nullptr, st);
+      return round([&](cudaStream_t q) {
+        return launch_receive_fused(*pl, y, pil, yd, nullptr, xx, nullptr, nullptr, nullptr, q);
+      });
     });
     if (ms < 0.f) {
-      pl->tiles.msplit = dflt;
-      return cuda_fail(cudaGetLastError(), "detector split during tuning");
+      status = cuda_fail(cudaGetLastError(), "fused receive during tuning");
+      break;
     }
-    if (best_ms < 0.f || ms < best_ms) {
-      best_split = split;
-      best_ms = ms;
-    }
+    consider(best_v, best_g, split, RAPRO_RECV_FUSED, ms);
   }
+  pl->est_variant = best_v;
+  pl->est_ctas_per_sm = best_g;
   pl->tiles.msplit = best_split;
-  pl->recv_form = RAPRO_RECV_SPLIT;
-  // The fused receive form against the tuned two-kernel form, where it applies.
-  if (receive_fused_ok(*pl, y_pilot, y_data)) {
-    const float split_ms = time_on(st, kWarm, kReps, [&] {
-      cudaError_t r = launch_lmmse(*pl, y, pil, pl->d_w_main, pl->d_w_tail, nullptr, nullptr, hh, st);
-      return r != cudaSuccess ? r : launch_detect(*pl, hh, yd, xx, nullptr, nullptr, nullptr, st);
-    });
-    if (split_ms < 0.f) return cuda_fail(cudaGetLastError(), "two-kernel receive during tuning");
-    int best_fused = -1;
-    float fused_ms = 0.f;
-    for (int split = 1; split <= dflt; ++split) {
-      pl->tiles.msplit = split;
-      const float ms = time_on(st, kWarm, kReps, [&] {
-        return launch_receive_fused(*pl, y, pil, yd, nullptr, xx, nullptr, nullptr, nullptr, st);
-      });
-      if (ms < 0.f) {
-        pl->tiles.msplit = best_split;
-        return cuda_fail(cudaGetLastError(), "fused receive during tuning");
-      }
-      if (best_fused < 0 || ms < fused_ms) {
-        best_fused = split;
-        fused_ms = ms;
-      }
-    }
-    if (fused_ms < split_ms) {
-      pl->recv_form = RAPRO_RECV_FUSED;
-      pl->tiles.msplit = best_fused;
-    } else {
-      pl->tiles.msplit = best_split;
-    }
+  pl->recv_form = best_form;
+  if (status == RAPRO_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) status = cuda_fail(e, "tuning");
   }
+  cleanup();
+  return status;
+}
+
+rapro_status rapro_plan_set_variant(rapro_plan* plan, int est_variant, int det_split, int est_ctas_per_sm) {
+  if (!plan) return bad("plan is NULL");
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  if (est_variant < -1 || est_variant >= EST_VARIANTS) return bad("est_variant must be -1 .. 3");
+  if (pl->comb && est_variant != -1) return bad("comb plans have one estimator (est_variant -1)");
+  const int max_split = make_det_tiles(pl->p.K, pl->D).msplit;
+  if (det_split < 1 || det_split > max_split) return bad("det_split out of range for this plan");
+  if (est_ctas_per_sm < 0 || est_ctas_per_sm > 8) return bad("est_ctas_per_sm must be 0 .. 8");
+  pl->est_variant = est_variant;
+  pl->tiles.msplit = det_split;
+  pl->est_ctas_per_sm = est_ctas_per_sm;
   return RAPRO_OK;
 }
 
@@ -173,11 +213,12 @@ rapro_status rapro_receive_is_fused(const rapro_plan* plan, const rapro_c32* y_p
   return RAPRO_OK;
 }
 
-rapro_status rapro_plan_variant(const rapro_plan* plan, int* est_variant, int* det_split) {
+rapro_status rapro_plan_variant(const rapro_plan* plan, int* est_variant, int* det_split, int* est_ctas_per_sm) {
   if (!plan) return bad("plan is NULL");
   const Plan* pl = reinterpret_cast<const Plan*>(plan);
   if (est_variant) *est_variant = pl->est_variant;
   if (det_split) *det_split = pl->tiles.msplit;
+  if (est_ctas_per_sm) *est_ctas_per_sm = pl->est_ctas_per_sm;
   return RAPRO_OK;
 }
 

@@ -50,6 +50,10 @@ struct Plan {
   void* d_w_tc = nullptr;          // tensor-core filter operand (canonical layout), or null
   int est_variant = -1;            // estimator kernel (EST_*), -1 = built-in choice; set by rapro_plan_tune
   int recv_form = RAPRO_RECV_SPLIT; // rapro_receive_form of rapro_receive_subframe
+  // Tensor-core estimator CTAs per SM (0: as many as fit).  One leaves each SM room for a
+  // detector CTA of the next subframe in flight (with one warp per detector role), which
+  // raises the throughput of pipelined subframes; set by rapro_plan_tune / _set_variant.
+  int est_ctas_per_sm = 1;
   int* d_fix = nullptr;            // precision form: FP64-fallback count, ticket, list [T n_sc]
   bool comb = false;               // comb pilot layout (Sec. II)
   std::vector<float2> w_comb;      // comb weights [sets][Q][Q][Q] (3W: 1 set, S-W: K sets)
@@ -106,6 +110,9 @@ cudaError_t prepare_lmmse_tc(int device);
 // Estimator kernels a plan can use (the autotuner times the ones that apply).
 enum { EST_TC = 0, EST_STREAM = 1, EST_SMALL = 2, EST_TILED = 3, EST_VARIANTS = 4 };
 bool lmmse_variant_ok(const Plan& pl, int v, const float2* x, const float2* pil, const float2* out);
+// Detector warps per role of a plan by default: one, so that a detector CTA and an estimator
+// CTA of another subframe in flight share an SM (registers allow it only then).
+constexpr int kDefaultDetSplit = 1;
 cudaError_t launch_lmmse_variant(const Plan& pl, int v, const float2* x, const float2* pil, float2* out,
                                  cudaStream_t st);
 // Tensor-core LS + LMMSE (even B <= 16 dividing n_sc, aligned arrays).

@@ -409,6 +409,7 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
     pl->tail = p->n_sc % p->subblock;
   }
   pl->tiles = make_det_tiles(p->K, pl->D);
+  pl->tiles.msplit = kDefaultDetSplit;
 
   auto to_c64 = [](const std::vector<double>& w) {
     std::vector<float2> o(w.size() / 2);

@@ -72,8 +72,9 @@ def lib() -> ctypes.CDLL:
         "rapro_ce_comb": ([_P, _P, _P, _P, _P], ctypes.c_int),
         "rapro_mse_backward": ([_P] * 12, ctypes.c_int),
         "rapro_plan_tune": ([_P] * 7, ctypes.c_int),
-        "rapro_plan_variant": ([_P, _P, _P], ctypes.c_int),
+        "rapro_plan_variant": ([_P, _P, _P, _P], ctypes.c_int),
         "rapro_plan_set_receive_form": ([_P, ctypes.c_int], ctypes.c_int),
+        "rapro_plan_set_variant": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "rapro_receive_is_fused": ([_P, _P, _P, _P], ctypes.c_int),
         "rapro_batch_create": ([ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
         "rapro_batch_destroy": ([_P], ctypes.c_int),
@@ -296,10 +297,16 @@ def rapro_plan_tune(plan: Plan, y_pilot, pilots, y_data, h, x_eq, stream=None) -
 
 
 def rapro_plan_variant(plan: Plan):
-    """(estimator kernel, detector warps per role) the plan uses."""
-    ev, ds = ctypes.c_int(), ctypes.c_int()
-    _check(lib().rapro_plan_variant(plan.handle, ctypes.byref(ev), ctypes.byref(ds)), "rapro_plan_variant")
-    return ev.value, ds.value
+    """(estimator kernel, detector warps per role, tensor-core estimator CTAs per SM)."""
+    ev, ds, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().rapro_plan_variant(plan.handle, ctypes.byref(ev), ctypes.byref(ds), ctypes.byref(g)),
+           "rapro_plan_variant")
+    return ev.value, ds.value, g.value
+
+
+def rapro_plan_set_variant(plan: Plan, est_variant: int, det_split: int, est_ctas_per_sm: int = 1) -> None:
+    _check(lib().rapro_plan_set_variant(plan.handle, int(est_variant), int(det_split), int(est_ctas_per_sm)),
+           "rapro_plan_set_variant")
 
 
 def rapro_plan_set_receive_form(plan: Plan, form: int) -> None:

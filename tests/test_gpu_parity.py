@@ -744,8 +744,8 @@ def test_autotuner_picks_an_applicable_kernel_and_keeps_parity(case):
     x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
     assert R.rapro_plan_variant(plan)[0] == -1
     R.rapro_plan_tune(plan, yp, pil, yd, h, x)
-    ev, split = R.rapro_plan_variant(plan)
-    assert ev in (0, 1, 2, 3) and split in (1, 2)
+    ev, split, grid = R.rapro_plan_variant(plan)
+    assert ev in (0, 1, 2, 3) and split in (1, 2) and grid in (0, 1)
     if B > 32:
         assert ev == 3
     if B > 16:
