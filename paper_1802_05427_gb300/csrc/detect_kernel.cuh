@@ -349,12 +349,17 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     }
     const float2* hsrc = st;                           // the chunk's h rows [KP][PL]
     if constexpr (FUSED) {
-      // LS + LMMSE of the chunk: half-warp g takes units u = (user u/2, antenna parity u%2)
-      // of 4 rows; lane sc owns output subcarrier k0 + sc.  The two half-warps of a warp
-      // read adjacent rows, which sit on different banks (span % 16 != 0).
+      // LS + LMMSE of the chunk: half-warp g takes a run of U consecutive units u = (user
+      // u/2, antenna parity u%2) of 4 rows, so that its users (and weight rows) change
+      // little; lane sc owns output subcarrier k0 + sc.  The two half-warps of a warp read
+      // adjacent rows, which sit on different banks (span % 16 != 0).
       float2* hb = hs + (c & 1) * KP * PL;
       if (!aborted) {
-        for (int u = warp * 2 + mh; u < 2 * K; u += 2 * n_cons) {
+        const int U = (2 * K + 2 * n_cons - 1) / (2 * n_cons), g = warp * 2 + mh;
+        for (int i = 0; i < U; ++i) {
+          // odd half-warps take each user's parities in the other order (adjacent rows again)
+          const int u = g * U + ((U & 1) ? i : (i ^ (g & 1)));
+          if (u >= 2 * K) continue;
           const int k = u >> 1, par = u & 1;
           if (k != cur_k) {
             const float4* wr = reinterpret_cast<const float4*>(wps + (k * DET_SC + sc) * 16);
