@@ -758,6 +758,38 @@ def test_autotuner_picks_an_applicable_kernel_and_keeps_parity(case):
     check_detection(dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr)), o, sh.qam_bits)
 
 
+@pytest.mark.parametrize("case", [(20, 12, 96, 128, 12), (16, 5, 100, 256, 10)])
+def test_every_kernel_choice_keeps_parity(case):
+    """Each estimator kernel that applies, one or two detector warps per role and one or as
+    many estimator CTAs per SM as fit: the same results as the oracle."""
+    M, K, N, nfft, B = case
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, snr_db=14.0, qam_bits=4)
+    sf, c64 = _inputs(sh, 21)
+    o = oracle_receive(sh, c64, B)
+    plan = R.Plan(params_for(sh, B))
+    s = plan.shapes()
+    assert R.rapro_plan_variant(plan) == (-1, 1, 1)                  # the throughput defaults
+    yp, pil, yd = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"])
+    for ev in (-1, 0, 1, 2, 3):
+        for split in (1, 2):
+            for grid in (0, 1):
+                R.rapro_plan_set_variant(plan, ev, split, grid)
+                assert R.rapro_plan_variant(plan) == (ev, split, grid)
+                h = torch.empty(s["h"], dtype=torch.complex64, device="cuda")
+                x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
+                lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
+                llr = torch.empty(s["llr"], dtype=torch.float32, device="cuda")
+                R.rapro_receive_subframe(plan, yp, pil, yd, x, lab, llr, h_out=h)
+                assert rel_err_per(_host(h), o["h"], axes=(2, 3)).max() <= TOL, (ev, split, grid)
+                check_detection(dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr)), o, sh.qam_bits)
+    for bad in ((4, 1, 1), (-2, 1, 1), (-1, 0, 1), (-1, 3, 1), (-1, 1, 9), (-1, 1, -1)):
+        with pytest.raises(R.RaproError):
+            R.rapro_plan_set_variant(plan, *bad)
+    assert R.rapro_plan_variant(plan) == (3, 2, 1)                   # a bad call changes nothing
+    assert plan.device_status() == 0
+    plan.close()
+
+
 def test_bf16_form_falls_back_to_fp64_on_ill_conditioned_subcarriers():
     """Users 0 and 1 nearly collinear on two subcarriers with a tiny sigma2: cond(A) ~ 1e8.
     The precision form re-solves those subcarriers in FP64 (agreeing with the FP64 oracle),
