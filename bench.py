@@ -580,14 +580,18 @@ def run_rapro(args):
                 torch.cuda.synchronize()
                 sweep[str(Bs)] = res_per_step * r2 * GRAPH_STEPS / (e0.elapsed_time(e1) * 1e-3)
 
-    # precision form: the sub-block filter as one BF16 pass on the tensor cores
+    # precision forms: the sub-block filter as one BF16 or FP16 pass on the tensor cores.  The
+    # detector of such a plan keeps its FP64-fallback list in the plan, so each pipeline
+    # stream gets a plan of its own.
     prec = {}
     if want("precision") and rank == 0 and world == 1 and B % 2 == 0 and B <= 16 and sh.n_sc % B == 0:
-        pb = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, sigma2=sh.sigma2,
-                           qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms, precision=R.RAPRO_PREC_BF16)
-        with R.Plan(pb) as plb:
+        for name, pv in (("bf16_tc", R.RAPRO_PREC_BF16), ("fp16_tc", R.RAPRO_PREC_FP16)):
+            pb = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, sigma2=sh.sigma2,
+                               qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms, precision=pv)
+            plbs = [R.Plan(pb) for _ in range(IN_FLIGHT)]
+
             def bstep(i, det=True, stream=None):
-                d, o = sets[i % N_SETS], outs[i % IN_FLIGHT]
+                d, o, plb = sets[i % N_SETS], outs[i % IN_FLIGHT], plbs[i % IN_FLIGHT]
                 R.rapro_ce_ls_lmmse(plb, d["y_pilot"], d["pilots"], o["h"], stream=stream)
                 if det:
                     R.rapro_mmse_detect(plb, o["h"], d["y_data"], o["x"], o["lab"], None, o["info"], stream=stream)
@@ -615,9 +619,11 @@ def run_rapro(args):
                 torch.cuda.synchronize()
                 gb.append(g)
             us_b_full, us_b_est = time_graph(gb[0], 64), time_graph(gb[1], 64)
-            prec["bf16_tc"] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est,
-                               "estimator_hbm_frac": alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)}
-            assert plb.device_status() == 0
+            prec[name] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est,
+                          "estimator_hbm_frac": alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)}
+            for plb in plbs:
+                assert plb.device_status() == 0
+                plb.close()
 
     # differentiable receive: forward + adjoint per subframe, and an Adam fit of (sigma2, tau)
     diff = {}

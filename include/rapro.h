@@ -24,7 +24,7 @@
  *  - No call throws across the ABI, traps on the device or asserts.  NaN/Inf inputs
  *    propagate to the outputs.  Calls that share a plan may run concurrently on
  *    different streams except rapro_receive_subframe with h_out == NULL, which writes
- *    the plan's workspace, and the detector of a RAPRO_PREC_BF16 plan, which keeps its
+ *    the plan's workspace, and the detector of a RAPRO_PREC_BF16 or _FP16 plan, which keeps its
  *    FP64-fallback list in the plan: serialise those per plan.
  *
  * Layouts (T = n_pilot_sym slots, D = n_sym / n_pilot_sym - 1 data symbols per slot):
@@ -110,7 +110,11 @@ typedef enum {
    * falls back to FP64 for every subcarrier whose FP32 Cholesky pivots give
    * (max L_jj / min L_jj)^2 > 1e6 (a lower bound of cond(A)) or fail: Eq. 22 solved again
    * in FP64 by an extra kernel, which overwrites that subcarrier's outputs and info. */
-  RAPRO_PREC_BF16 = 1
+  RAPRO_PREC_BF16 = 1,
+  /* As RAPRO_PREC_BF16 with FP16 operands (11 significant bits, range +-65504: relative
+   * filter error ~ 2^-10 for the O(1) LS estimates and weights of unit-power channels);
+   * the same rules and the same FP64 detector fallback. */
+  RAPRO_PREC_FP16 = 2
 } rapro_precision;
 
 /* How rapro_receive_subframe runs a subframe (no counterpart in the paper, which runs the
@@ -286,7 +290,7 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
  * (tensor cores with one or as many CTAs per SM as fit, streaming, row-segment and tiled
  * kernels; comb plans have one), the detector's warps per role and (where it applies) the
  * fused receive form, each as whole receives with four subframes in flight on streams of
- * the library's (one at a time for RAPRO_PREC_BF16 plans), 2 warm and 5 timed rounds, and
+ * the library's (one at a time for BF16 and FP16 plans), 2 warm and 5 timed rounds, and
  * keeps the one with the best throughput in the plan (later calls with arrays a choice does
  * not apply to fall back to the built-in choice).  Overwrites h and x_eq.  Synchronises the stream; not inside a
  * stream capture.  The plan must not be in use by another stream meanwhile.

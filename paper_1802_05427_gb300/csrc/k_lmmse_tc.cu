@@ -32,6 +32,7 @@
 #include <vector>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "rapro_internal.h"
 #include "rapro_ptx.cuh"
@@ -49,33 +50,50 @@ constexpr int TC_THREADS = TC_CONSUMERS + 64;   // + one MMA warp + one copy war
 // The TF32 passes use the shared M = 128, N = 32 instruction (rapro_ptx.cuh).
 static_assert(TC_ROWS == 128 && TC_N == 32, "the TF32 MMA helper is M = 128, N = 32");
 
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = TC_N.
+// Operand forms of the filter: three TF32 passes (FP32 accuracy) or one pass of 16-bit
+// operands, both A and B in the same format (BF16 or FP16), FP32 accumulation.
+enum { OP_TF32X3 = 0, OP_BF16 = 1, OP_FP16 = 2 };
+
+// Instruction descriptors: D = F32, A = B = BF16 (format 1) or FP16 (format 0), both
+// K-major, M = 128, N = TC_N.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TC_N >> 3) << 17) |
                                 (uint32_t(TC_ROWS >> 4) << 24);
+constexpr uint32_t kIdescFp16 = (1u << 4) | (0u << 7) | (0u << 10) | (uint32_t(TC_N >> 3) << 17) |
+                                (uint32_t(TC_ROWS >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
+template <uint32_t IDESC>
+__device__ __forceinline__ void mma_f16kind(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate ? 1 : 0)
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate ? 1 : 0)
       : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (lower address) = lo
-  return *reinterpret_cast<const uint32_t*>(&v);
+// Two floats rounded to nearest even into one 32-bit word, the first at the lower address.
+template <int OP>
+__device__ __forceinline__ uint32_t pack16x2(float lo, float hi) {
+  if constexpr (OP == OP_FP16) {
+    const __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  } else {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
 }
 
 }  // namespace
 
-// KR: reals per row-block, 2B padded to the MMA's K step (8 for TF32, 16 for BF16).
-// BF: one BF16 pass (the precision form) instead of the three TF32 passes.
-template <int KR, bool BF>
+// KR: reals per row-block, 2B padded to the MMA's K step (8 for TF32, 16 for 16-bit).
+// OP: the operand form; OP_BF16 / OP_FP16 is one 16-bit pass (the precision form) instead
+// of the three TF32 passes.
+template <int KR, int OP>
 __global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* __restrict__ y,
                                                               const float2* __restrict__ pil,
                                                               float2* __restrict__ out, int M, int N, int B,
                                                               long long n_rb, int n_tiles, int* status,
                                                               const void* __restrict__ w_tc) {
+  constexpr bool BF = OP != OP_TF32X3;                          // one 16-bit pass
   static_assert(KR % (BF ? 16 : 8) == 0 && KR <= 32, "2B padded to the K step, at most 32");
   constexpr int ELT = BF ? 2 : 4;                               // operand bytes
   constexpr int CE = 16 / ELT;                                  // operand elements per 16-byte core row
@@ -199,7 +217,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* _
         for (int kg = 0; kg < KSTEPS; ++kg) {
           const uint64_t dah = smem_desc_kmajor(ah + kg * 256, 128, SBO), dbh = smem_desc_kmajor(sBh + kg * 256, 128, SBO);
           if (BF) {
-            mma_bf16(d, dah, dbh, kg > 0);
+            mma_f16kind<OP == OP_FP16 ? kIdescFp16 : kIdescBf16>(d, dah, dbh, kg > 0);
           } else {
             const uint64_t dal = smem_desc_kmajor(al + kg * 256, 128, SBO);
             const uint64_t dbl = smem_desc_kmajor(sBh + B_BYTES + kg * 256, 128, SBO);
@@ -258,8 +276,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* _
 #pragma unroll
         for (int j = 0; j < KH; j += 2) {
           const int c = (half * KH + j) / 2;
-          const uint4 v = make_uint4(pack_bf16x2(q[j].x, q[j].y), pack_bf16x2(q[j].z, q[j].w),
-                                     pack_bf16x2(q[j + 1].x, q[j + 1].y), pack_bf16x2(q[j + 1].z, q[j + 1].w));
+          const uint4 v = make_uint4(pack16x2<OP>(q[j].x, q[j].y), pack16x2<OP>(q[j].z, q[j].w),
+                                     pack16x2<OP>(q[j + 1].x, q[j + 1].y), pack16x2<OP>(q[j + 1].z, q[j + 1].w));
           *reinterpret_cast<uint4*>(ah + (r / 8) * SBO + c * 128 + (r % 8) * 16) = v;
         }
       } else {
@@ -331,9 +349,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* _
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N) : "memory");
 }
 
-template <int KR, bool BF>
+template <int KR, int OP>
 static size_t tc_smem_bytes(int B) {
-  const size_t elt = BF ? 2 : 4, na = BF ? 1 : 2;
+  const size_t elt = OP != OP_TF32X3 ? 2 : 4, na = OP != OP_TF32X3 ? 1 : 2;
   return 1024 + 2 * na * size_t(TC_ROWS) * KR * elt + na * size_t(TC_N) * KR * elt +
          size_t(TC_STAGES) * TC_ROWS * B * sizeof(float2);
 }
@@ -349,6 +367,25 @@ static float tf32_host(float x) {
   return r;
 }
 
+// Round to nearest even at FP16 (10 explicit mantissa bits, subnormals below 2^-14,
+// overflow to infinity).
+static uint16_t f16_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  const uint32_t sign = (u >> 16) & 0x8000u, a = u & 0x7fffffffu;
+  if (a > 0x7f800000u) return uint16_t(sign | 0x7e00u);               // NaN
+  if (a >= 0x47800000u) return uint16_t(sign | 0x7c00u);              // |x| >= 65536: inf
+  if (a < 0x38800000u) {                                               // |x| < 2^-14
+    float f;
+    std::memcpy(&f, &a, 4);
+    return uint16_t(sign | uint32_t(std::nearbyint(f * 16777216.0f)));   // units of 2^-24, ties even
+  }
+  uint32_t h = (a - 0x38000000u) >> 13;                                // rebias 127 -> 15
+  const uint32_t rem = a & 0x1fffu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;              // may carry into the exponent
+  return uint16_t(sign | (h >= 0x7c00u ? 0x7c00u : h));
+}
+
 static uint16_t bf16_host(float x) {
   // Round to nearest even at 7 explicit mantissa bits (finite inputs).
   uint32_t u;
@@ -358,9 +395,9 @@ static uint16_t bf16_host(float x) {
 }
 
 // Reals per row-block: 2B padded to the K step (8 for TF32, 16 for BF16).
-static int kr_for(int B, bool bf) { return bf ? (2 * B + 15) / 16 * 16 : (2 * B + 7) / 8 * 8; }
+static int kr_for(int B, bool half) { return half ? (2 * B + 15) / 16 * 16 : (2 * B + 7) / 8 * 8; }
 
-template <int KR, bool BF>
+template <int KR, int OP>
 static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
   const int B = pl.B, M = pl.p.M, N = pl.p.n_sc, R = pl.T * pl.p.K * pl.p.M;
   const long long n_rb = (long long)R * (N / B);
@@ -370,17 +407,17 @@ static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  const size_t smem = tc_smem_bytes<KR, BF>(B);
+  const size_t smem = tc_smem_bytes<KR, OP>(B);
   // Resident CTAs per SM: shared memory, threads (2048 per SM), registers (64 K, allocated
   // per warp in units of 8 per thread) and tensor memory (512 columns).
   cudaFuncAttributes fa{};
-  cudaFuncGetAttributes(&fa, lmmse_tc_kernel<KR, BF>);
+  cudaFuncGetAttributes(&fa, lmmse_tc_kernel<KR, OP>);
   const int regs_warp = ((std::max(fa.numRegs, 1) + 7) / 8 * 8) * 32;
   int per_sm = int(size_t(smem_sm) / (smem + size_t(reserved)));
   per_sm = std::max(1, std::min({per_sm, 2048 / TC_THREADS, 512 / (2 * TC_N), 65536 / (regs_warp * (TC_THREADS / 32))}));
   if (pl.est_ctas_per_sm > 0) per_sm = std::min(per_sm, pl.est_ctas_per_sm);
   const int grid = std::min(n_tiles, per_sm * sms);
-  lmmse_tc_kernel<KR, BF><<<grid, TC_THREADS, smem, st>>>(y, pil, out, M, N, B, n_rb, n_tiles, pl.d_status,
+  lmmse_tc_kernel<KR, OP><<<grid, TC_THREADS, smem, st>>>(y, pil, out, M, N, B, n_rb, n_tiles, pl.d_status,
                                                             pl.d_w_tc);
   return cudaGetLastError();
 }
@@ -392,9 +429,9 @@ bool lmmse_tc_shape_ok(const Plan& pl) {
 }
 
 // The filter as the MMA's B operand: Wr (TC_N x KR reals, zero padded) in the canonical
-// K-major layout: TF32 hi part followed by its lo part, or one BF16 part (as raw bytes).
+// K-major layout: TF32 hi part followed by its lo part, or one BF16 / FP16 part (raw bytes).
 void build_lmmse_tc_weights(const Plan& pl, std::vector<unsigned char>& out) {
-  const bool bf = pl.p.precision == RAPRO_PREC_BF16;
+  const bool bf = half_precision(pl.p), f16 = pl.p.precision == RAPRO_PREC_FP16;
   const int B = pl.B, KR = kr_for(B, bf), elt = bf ? 2 : 4, ce = 16 / elt;
   const int SBO = (KR / ce) * 128, part = TC_N * KR * elt;
   out.assign(size_t(bf ? 1 : 2) * part, 0);
@@ -408,7 +445,7 @@ void build_lmmse_tc_weights(const Plan& pl, std::vector<unsigned char>& out) {
           const size_t off = size_t((n / 8) * SBO + (k / ce) * 128 + (n % 8) * 16 + (k % ce) * elt);
           const float f = vals[a][c];
           if (bf) {
-            const uint16_t h = bf16_host(f);
+            const uint16_t h = f16 ? f16_host(f) : bf16_host(f);
             std::memcpy(&out[off], &h, 2);
           } else {
             const float h = tf32_host(f), l = tf32_host(f - h);
@@ -427,12 +464,16 @@ bool lmmse_tc_ok(const Plan& pl, const float2* y, const float2* pil, const float
 
 cudaError_t launch_lmmse_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
   if (pl.p.precision == RAPRO_PREC_BF16)
-    return kr_for(pl.B, true) == 16 ? launch_tc<16, true>(pl, y, pil, out, st) : launch_tc<32, true>(pl, y, pil, out, st);
+    return kr_for(pl.B, true) == 16 ? launch_tc<16, OP_BF16>(pl, y, pil, out, st)
+                                    : launch_tc<32, OP_BF16>(pl, y, pil, out, st);
+  if (pl.p.precision == RAPRO_PREC_FP16)
+    return kr_for(pl.B, true) == 16 ? launch_tc<16, OP_FP16>(pl, y, pil, out, st)
+                                    : launch_tc<32, OP_FP16>(pl, y, pil, out, st);
   switch (kr_for(pl.B, false)) {
-    case 8: return launch_tc<8, false>(pl, y, pil, out, st);
-    case 16: return launch_tc<16, false>(pl, y, pil, out, st);
-    case 24: return launch_tc<24, false>(pl, y, pil, out, st);
-    default: return launch_tc<32, false>(pl, y, pil, out, st);
+    case 8: return launch_tc<8, OP_TF32X3>(pl, y, pil, out, st);
+    case 16: return launch_tc<16, OP_TF32X3>(pl, y, pil, out, st);
+    case 24: return launch_tc<24, OP_TF32X3>(pl, y, pil, out, st);
+    default: return launch_tc<32, OP_TF32X3>(pl, y, pil, out, st);
   }
 }
 
@@ -442,12 +483,21 @@ cudaError_t prepare_lmmse_tc(int device) {
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   std::call_once(flags[device], [device] {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(lmmse_tc_kernel<8, false>, A, int(tc_smem_bytes<8, false>(4)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<16, false>, A, int(tc_smem_bytes<16, false>(8)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<24, false>, A, int(tc_smem_bytes<24, false>(12)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<32, false>, A, int(tc_smem_bytes<32, false>(16)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<16, true>, A, int(tc_smem_bytes<16, true>(8)));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tc_kernel<32, true>, A, int(tc_smem_bytes<32, true>(16)));
+    cudaError_t e = cudaFuncSetAttribute(lmmse_tc_kernel<8, OP_TF32X3>, A, int(tc_smem_bytes<8, OP_TF32X3>(4)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lmmse_tc_kernel<16, OP_TF32X3>, A, int(tc_smem_bytes<16, OP_TF32X3>(8)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lmmse_tc_kernel<24, OP_TF32X3>, A, int(tc_smem_bytes<24, OP_TF32X3>(12)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lmmse_tc_kernel<32, OP_TF32X3>, A, int(tc_smem_bytes<32, OP_TF32X3>(16)));
+    for (int op : {int(OP_BF16), int(OP_FP16)}) {
+      if (e != cudaSuccess) break;
+      e = op == OP_BF16 ? cudaFuncSetAttribute(lmmse_tc_kernel<16, OP_BF16>, A, int(tc_smem_bytes<16, OP_BF16>(8)))
+                        : cudaFuncSetAttribute(lmmse_tc_kernel<16, OP_FP16>, A, int(tc_smem_bytes<16, OP_FP16>(8)));
+      if (e == cudaSuccess)
+        e = op == OP_BF16 ? cudaFuncSetAttribute(lmmse_tc_kernel<32, OP_BF16>, A, int(tc_smem_bytes<32, OP_BF16>(16)))
+                          : cudaFuncSetAttribute(lmmse_tc_kernel<32, OP_FP16>, A, int(tc_smem_bytes<32, OP_FP16>(16)));
+    }
     result[device] = e;
   });
   return result[device];

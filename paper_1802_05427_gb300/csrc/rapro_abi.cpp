@@ -34,17 +34,18 @@ rapro_status orthogonal_only(const Plan* pl) {
   return RAPRO_ERR_UNSUPPORTED;
 }
 
-// The BF16 form runs only on the tensor-core estimator: LS fused, the plan's weights, aligned arrays.
+// The BF16 / FP16 forms run only on the tensor-core estimator: LS fused, the plan's
+// weights, aligned arrays.
 rapro_status bf16_check(const Plan* pl, const void* y, const void* pil, const void* h, const void* w_override) {
-  if (pl->p.precision != RAPRO_PREC_BF16) return RAPRO_OK;
+  if (!half_precision(pl->p)) return RAPRO_OK;
   if (!pil || w_override) {
-    set_error("the BF16 form needs the fused LS (pilots) and the plan's weights");
+    set_error("the BF16 / FP16 forms need the fused LS (pilots) and the plan's weights");
     return RAPRO_ERR_UNSUPPORTED;
   }
   const uintptr_t a = reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(pil) |
                       reinterpret_cast<uintptr_t>(h);
   if (a & 15) {
-    set_error("the BF16 form needs 16-byte aligned y_pilot, pilots and h");
+    set_error("the BF16 / FP16 forms need 16-byte aligned y_pilot, pilots and h");
     return RAPRO_ERR_INVALID_ARG;
   }
   return RAPRO_OK;

@@ -62,6 +62,11 @@ struct Plan {
   int device = 0;
 };
 
+// The precision forms with 16-bit filter operands (BF16 or FP16 on the tensor cores).
+inline bool half_precision(const rapro_params& p) {
+  return p.precision == RAPRO_PREC_BF16 || p.precision == RAPRO_PREC_FP16;
+}
+
 // Thread-local last-error text.
 void set_error(const std::string& msg);
 rapro_status cuda_fail(cudaError_t e, const char* what);

@@ -258,10 +258,10 @@ rapro_status rapro_params_validate(const rapro_params* p) {
     return invalid("unknown pdp kind");
   }
   if (p->qam_bits != 2 && p->qam_bits != 4 && p->qam_bits != 6) return invalid("qam_bits must be 2, 4 or 6");
-  if (p->precision == RAPRO_PREC_BF16) {
+  if (half_precision(*p)) {
     if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL || p->subblock % 2 != 0 || p->subblock > 16 ||
         p->n_sc % p->subblock != 0) {
-      set_error("the BF16 form filters on the tensor cores: orthogonal pilots, even subblock <= 16 dividing n_sc");
+      set_error("the BF16 / FP16 forms filter on the tensor cores: orthogonal pilots, even subblock <= 16 dividing n_sc");
       return RAPRO_ERR_UNSUPPORTED;
     }
   } else if (p->precision != RAPRO_PREC_FP32) {
@@ -472,7 +472,7 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if (pl->tail && (e = cudaMemcpy(pl->d_w_tail, pl->w_tail.data(), pl->w_tail.size() * sizeof(float2),
                                   cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "cudaMemcpy W tail");
   if ((e = cudaMemset(pl->d_status, 0, sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset status");
-  if (p->precision == RAPRO_PREC_BF16) {
+  if (half_precision(*p)) {
     if ((e = cudaMalloc(&pl->d_fix, (2 + size_t(pl->T) * p->n_sc) * sizeof(int))) != cudaSuccess)
       return fail(e, "cudaMalloc FP64-fallback list");
     if ((e = cudaMemset(pl->d_fix, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset FP64-fallback count");

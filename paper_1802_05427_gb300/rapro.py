@@ -22,7 +22,7 @@ RAPRO_ERR_TIMEOUT, RAPRO_ERR_UNSUPPORTED, RAPRO_ERR_NOMEM = 4, 5, 6
 RAPRO_PILOT_ORTHOGONAL, RAPRO_PILOT_COMB = 0, 1
 RAPRO_PDP_EXP, RAPRO_PDP_UNIFORM_L = 0, 1
 RAPRO_COMB_3W, RAPRO_COMB_SW, RAPRO_COMB_INTERP3 = 0, 1, 2
-RAPRO_PREC_FP32, RAPRO_PREC_BF16 = 0, 1
+RAPRO_PREC_FP32, RAPRO_PREC_BF16, RAPRO_PREC_FP16 = 0, 1, 2
 RAPRO_RECV_SPLIT, RAPRO_RECV_FUSED = 0, 1
 RAPRO_MAX_PILOT_SYM = 8
 

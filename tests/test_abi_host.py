@@ -143,6 +143,11 @@ def test_precision_validation(lib):
     for B in (7, 48, 13):                  # odd, > 16, not dividing 1200
         p.subblock = B
         assert R.rapro_params_validate(p) == R.RAPRO_ERR_UNSUPPORTED
+    p.subblock, p.precision = 12, R.RAPRO_PREC_FP16
+    assert R.rapro_params_validate(p) == R.RAPRO_OK
+    for B in (7, 48, 13):
+        p.subblock = B
+        assert R.rapro_params_validate(p) == R.RAPRO_ERR_UNSUPPORTED
     p.subblock, p.precision = 12, 5
     assert R.rapro_params_validate(p) == R.RAPRO_ERR_INVALID_ARG
 

@@ -502,35 +502,43 @@ def test_comb_and_orthogonal_plans_reject_each_others_estimators():
 # each) and accumulates in FP32: per output |err| <= sum_j |W_ij| |x_j| (2^-8 + 2^-16), so
 # norm-wise about 2^-8 / sqrt(3) for random signs; the bound below is 2^-7.
 TOL_BF16 = 2.0 ** -7
+# FP16 keeps 11 significant bits (unit roundoff 2^-11): the same argument gives 2^-9.
+TOL_FP16 = 2.0 ** -9
+HALF_FORMS = {"bf16": (R.RAPRO_PREC_BF16, TOL_BF16), "fp16": (R.RAPRO_PREC_FP16, TOL_FP16)}
 
 
+@pytest.mark.parametrize("form", list(HALF_FORMS))
 @pytest.mark.parametrize("case", [(8, 2, 72, 128, 12), (5, 3, 100, 256, 10), (6, 2, 96, 128, 16),
                                   (2, 1, 64, 128, 2), (128, 12, 1200, 2048, 12)])
-def test_bf16_estimator_parity(case):
+def test_bf16_estimator_parity(case, form):
     M, K, N, nfft, B = case
     sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=24 if nfft >= 2048 else 6,
                              tau_rms=8.0 if nfft >= 2048 else 4.0, snr_db=10.0, qam_bits=2)
     sf, c64 = _inputs(sh, 5)
+    prec, tol = HALF_FORMS[form]
     p = params_for(sh, B)
-    p.precision = R.RAPRO_PREC_BF16
+    p.precision = prec
     plan = R.Plan(p)
     h = torch.empty(plan.shapes()["h"], dtype=torch.complex64, device="cuda")
     R.rapro_ce_ls_lmmse(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), h)
     h_ls = O.ls_estimate(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128))
     ref = O.subblock_lmmse(h_ls, B, oracle_r(sh), sh.sigma2)
     e = rel_err_per(_host(h), ref, axes=(2, 3))
-    assert e.max() <= TOL_BF16, e.max()
-    assert e.max() > 1e-5                  # it really is the single BF16 pass
+    assert e.max() <= tol, e.max()
+    assert e.max() > 1e-5                  # it really is the single 16-bit pass
+    if form == "fp16":
+        assert e.max() < TOL_BF16 / 4      # and FP16's three extra bits show
     with pytest.raises(R.RaproError):
         R.rapro_ce_lmmse_subblock(plan, _dev(synth.as_c64(h_ls)), h)
 
 
-def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db():
-    """Precision form on the paper-scale shape (64-QAM, 25 dB, several subframes): channel
+@pytest.mark.parametrize("form", list(HALF_FORMS))
+def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db(form):
+    """Precision forms on the paper-scale shape (64-QAM, 25 dB, several subframes): channel
     NMSE and post-detection EVM within 0.1 dB of the FP64 oracle's."""
     sh = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "snr_db": 25.0, "qam_bits": 6})
     p = params_for(sh, 12)
-    p.precision = R.RAPRO_PREC_BF16
+    p.precision = HALF_FORMS[form][0]
     plan = R.Plan(p)
     s = plan.shapes()
     err_h = err_h_o = pow_h = err_x = err_x_o = pow_x = 0.0
@@ -806,7 +814,7 @@ def test_bf16_form_falls_back_to_fp64_on_ill_conditioned_subcarriers():
     x_o, _ = O.mmse_detect(h.astype(np.complex128), c64["y_data"].astype(np.complex128), sh.sigma2,
                            sh.n_data_per_slot)
     out = {}
-    for prec in (R.RAPRO_PREC_BF16, R.RAPRO_PREC_FP32):
+    for prec in (R.RAPRO_PREC_BF16, R.RAPRO_PREC_FP16, R.RAPRO_PREC_FP32):
         p = params_for(sh, 8)
         p.precision = prec
         plan = R.Plan(p)
@@ -815,12 +823,13 @@ def test_bf16_form_falls_back_to_fp64_on_ill_conditioned_subcarriers():
         info = torch.full(s["info"], -7, dtype=torch.int32, device="cuda")
         R.rapro_mmse_detect(plan, _dev(h), _dev(c64["y_data"]), x, info=info)
         out[prec] = (_host(x), _host(info))
-    x_b, info_b = out[R.RAPRO_PREC_BF16]
-    assert (info_b == 0).all()
-    e_b = rel_err_per(x_b, x_o, axes=(0, 1))                  # per subcarrier
-    assert e_b[bad].max() <= 1e-5, e_b[bad]
     good = np.setdiff1d(np.arange(sh.n_sc), bad)
-    assert e_b[good].max() <= 1e-4
+    for prec in (R.RAPRO_PREC_BF16, R.RAPRO_PREC_FP16):
+        x_b, info_b = out[prec]
+        assert (info_b == 0).all()
+        e_b = rel_err_per(x_b, x_o, axes=(0, 1))              # per subcarrier
+        assert e_b[bad].max() <= 1e-5, e_b[bad]
+        assert e_b[good].max() <= 1e-4
     x_f, _ = out[R.RAPRO_PREC_FP32]
     assert rel_err_per(x_f, x_o, axes=(0, 1))[bad].min() > 1e-3 or not np.isfinite(x_f[..., bad]).all()
 
