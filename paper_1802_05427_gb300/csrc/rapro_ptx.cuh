@@ -7,9 +7,11 @@
 
 namespace rapro {
 
-// A wait gives up after this many try_wait rounds (each round may suspend the thread
-// for a hardware-chosen interval); far beyond any legitimate latency.
+// A wait gives up after this many try_wait rounds; each round suspends the thread until the
+// phase completes or at most kSuspendHintNs pass, so a waiting warp takes few issue slots
+// from the warps (and co-resident CTAs) that work, and a wait ends within about 2 s.
 constexpr uint32_t kSpinLimit = 1u << 20;
+constexpr uint32_t kSuspendHintNs = 2000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -36,10 +38,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "n"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
