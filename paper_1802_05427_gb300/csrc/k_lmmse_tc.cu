@@ -240,12 +240,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) lmmse_tc_kernel(const float2* _
   } else {
     // ------------------------------------------------ consumers: LS + split, read-back
     const int r = tid & (TC_ROWS - 1), half = tid / TC_ROWS;   // row-block of the tile, half of it
-    // Pilots of this thread's row-block of tile it (B complex, two per float4).
+    // This thread's row-block of tile it: rb = row * nb + b, row = tk * M + m (tk = slot-user).
+    // Tiles of a CTA are consecutive, so rb advances by TC_ROWS per tile and the quotients are
+    // carried along instead of divided again (a division only when m passes M).
+    uint32_t p_b = 0, p_tk = 0, p_m = 0;
+    const uint32_t q_rows = uint32_t(TC_ROWS) / uint32_t(nb), r_rows = uint32_t(TC_ROWS) % uint32_t(nb);
+    {
+      const uint32_t rb0 = uint32_t(tile_of(0)) * TC_ROWS + uint32_t(r);   // n_rb < 2^31
+      const uint32_t row0 = rb0 / uint32_t(nb);
+      p_b = rb0 - row0 * uint32_t(nb);
+      p_tk = row0 / uint32_t(M);
+      p_m = row0 - p_tk * uint32_t(M);
+    }
+    auto advance_row_block = [&]() {
+      p_b += r_rows;
+      uint32_t dr = q_rows;
+      if (p_b >= uint32_t(nb)) {
+        p_b -= uint32_t(nb);
+        ++dr;
+      }
+      p_m += dr;
+      if (p_m >= uint32_t(M)) {
+        p_tk += p_m / uint32_t(M);
+        p_m %= uint32_t(M);
+      }
+    };
+    // Pilots of this thread's row-block of tile it (B complex, two per float4); called for
+    // it = 0, 1, 2, ... in order, each call after the first moving on by one tile.
     auto load_pilots = [&](int it, float4 (&pv)[KH]) {
+      if (it > 0) advance_row_block();
       if (it >= my_tiles || r >= tile_count(it)) return;
-      const uint32_t rb = uint32_t(tile_of(it)) * TC_ROWS + uint32_t(r);   // n_rb < 2^31
-      const uint32_t row = rb / uint32_t(nb), b = rb - row * uint32_t(nb);
-      const float4* pr = reinterpret_cast<const float4*>(pil + size_t(row / uint32_t(M)) * N + size_t(b) * B);
+      const float4* pr = reinterpret_cast<const float4*>(pil + size_t(p_tk) * N + size_t(p_b) * B);
 #pragma unroll
       for (int j = 0; j < KH; ++j) {
         const int kg = half * KH + j;
