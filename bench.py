@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--subblock", type=int, default=12)
     ap.add_argument("--snr", type=float, default=10.0)
     ap.add_argument("--no-sweep", action="store_true", help="skip every extra section")
-    ap.add_argument("--sections", default="sweep,precision,differentiable,hetero,comb",
+    ap.add_argument("--sections", default="sweep,precision,differentiable,hetero,comb,batch64",
                     help="extra sections after the headline line's measurement (comma list)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
@@ -684,6 +684,39 @@ def run_rapro(args):
     if want("hetero") and rank == 0 and world == 1:
         hetero = hetero_batch(dev)
 
+    # 64 paper-scale subframes in one rapro_receive_batch call (one plan, 8 library streams,
+    # one CUDA graph per batch; the inputs rotate over the resident sets, every job has its
+    # own outputs)
+    batch64 = {}
+    if want("batch64") and rank == 0 and world == 1:
+        n64 = 64
+        jobs64 = [dict(plan=plan, y_pilot=sets[i % N_SETS]["y_pilot"], pilots=sets[i % N_SETS]["pilots"],
+                       y_data=sets[i % N_SETS]["y_data"], h_out=torch.empty(s["h"], dtype=torch.complex64, device=dev),
+                       x_eq=torch.empty(s["x_eq"], dtype=torch.complex64, device=dev),
+                       labels=torch.empty(s["labels"], dtype=torch.uint8, device=dev)) for i in range(n64)]
+        b64 = R.Batch(8)
+        R.rapro_receive_batch(b64, jobs64)
+        torch.cuda.synchronize()
+        g64 = torch.cuda.CUDAGraph()
+        st64 = torch.cuda.Stream()
+        st64.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st64):
+            with torch.cuda.graph(g64, stream=st64):
+                R.rapro_receive_batch(b64, jobs64, stream=st64)
+        g64.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(8):
+            g64.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / 8
+        b64.close()
+        assert plan.device_status() == 0
+        batch64 = {"subframes": n64, "ms_per_batch": ms64, "res_per_s": n64 * res_per_step / (ms64 * 1e-3),
+                   "api": "rapro_receive_batch, 8 streams, one CUDA graph per batch"}
+        del jobs64
+
     # comb pilots (Sec. II, IV-B) on the same 128 x 12 x 1200 shape: 12W, 3W, interpolated LS
     comb = {}
     if want("comb") and rank == 0 and world == 1:
@@ -790,7 +823,7 @@ def run_rapro(args):
                                               "stream, same plan variant as the timed step",
             "sweep_res_per_s": sweep, "user_symbols_per_s": value * sh.K,
             "comb_pilots": comb, "precision_form": prec, "differentiable": diff,
-            "batched_heterogeneous": hetero}
+            "batched_heterogeneous": hetero, "batch_of_64_subframes": batch64}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
