@@ -287,8 +287,8 @@ rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_p
 /*
  * Autotuner (no counterpart in the paper, whose receiver has one code path): times every
  * combination of the estimator kernels that apply to the plan's shape and these arrays
- * (tensor cores with one or as many CTAs per SM as fit, streaming, row-segment and tiled
- * kernels; comb plans have one), the detector's warps per role and (where it applies) the
+ * (tensor cores with one or as many CTAs per SM as fit, the tensor-core GEMM for large
+ * blocks, streaming, row-segment and tiled kernels; comb plans have one), the detector's warps per role and (where it applies) the
  * fused receive form, each as whole receives with four subframes in flight on streams of
  * the library's (one at a time for BF16 and FP16 plans), 2 warm and 5 timed rounds, and
  * keeps the one with the best throughput in the plan (later calls with arrays a choice does
@@ -299,14 +299,15 @@ rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const r
                              const rapro_c32* y_data, rapro_c32* h, rapro_c32* x_eq, rapro_stream stream);
 
 /* The plan's kernel choices: estimator kernel (-1 built-in, 0 tensor cores, 1 streaming,
- * 2 row segments, 3 tiled), the detector's warps per role, and the tensor-core estimator's
+ * 2 row segments, 3 tiled, 4 tensor-core GEMM for even 16 < B <= 2048 dividing n_sc), the detector's
+ * warps per role, and the tensor-core estimator's
  * CTAs per SM (0: as many as fit).  A new plan has -1, 1 and 1: one warp per role and one
  * estimator CTA per SM leave room on every SM for an estimator and a detector CTA of two
  * subframes in flight.  Any pointer may be NULL. */
 rapro_status rapro_plan_variant(const rapro_plan* plan, int* est_variant, int* det_split, int* est_ctas_per_sm);
 
 /* Set the plan's kernel choices by hand (as rapro_plan_tune would): est_variant -1 (built-in)
- * or 0..3 as above (a choice that does not apply to later calls' arrays falls back to the
+ * or 0..4 as above (a choice that does not apply to later calls' arrays falls back to the
  * built-in one), det_split 1 or 2 (at most 2 when the detector has at most 8 roles, else 1),
  * est_ctas_per_sm 0..8.  RAPRO_ERR_INVALID_ARG otherwise.  Not while another stream uses the
  * plan. */

@@ -440,6 +440,7 @@ bool lmmse_variant_ok(const Plan& pl, int v, const float2* x, const float2* pil,
     case EST_STREAM: return pil && pl.B <= LMMSE_SMALL_MAX && stream_ok(x, pil, out, pl.p.n_sc, pl.B, pl.nb);
     case EST_SMALL: return pl.B <= LMMSE_SMALL_MAX;
     case EST_TILED: return true;
+    case EST_TCG: return lmmse_tcg_ok(pl, x, out);
     default: return false;
   }
 }
@@ -451,9 +452,11 @@ cudaError_t launch_lmmse_variant(const Plan& pl, int v, const float2* x, const f
   if (v < 0 || !lmmse_variant_ok(pl, v, x, pil, out)) {
     if (lmmse_tc_ok(pl, x, pil, out)) return launch_lmmse_tc(pl, x, pil, out, st);
     if (half_precision(pl.p)) return cudaErrorNotSupported;   // never a silent FP32 fallback
+    if (lmmse_tcg_ok(pl, x, out)) return launch_lmmse_tcg(pl, x, pil, out, st);
     v = pl.B <= LMMSE_SMALL_MAX ? EST_STREAM : EST_TILED;
   }
   if (v == EST_TC) return launch_lmmse_tc(pl, x, pil, out, st);
+  if (v == EST_TCG) return launch_lmmse_tcg(pl, x, pil, out, st);
   if (v == EST_TILED) return launch_tiled(pl, x, pil, pl.d_w_main, pl.d_w_tail, 0, out, st);
   const bool stream = v == EST_STREAM;
   const int B = pl.B;

@@ -1,0 +1,506 @@
+// LS + sub-block LMMSE (Eq. 9, 12, 17) for large blocks as a GEMM on the 5th-generation
+// tensor cores (tcgen05), FP32 accuracy from three TF32 passes.
+//
+// With B dividing n_sc all blocks share W, and block b of every row r = (slot, user,
+// antenna) is one row of the product
+//   H_b = X_b W^T (complex)  =  X_r,b Wr^T  in the interleaved real embedding,
+// K = 2B input reals, N = 2B output reals (Wr as in k_lmmse_tc.cu).  For B > 16 the whole
+// W no longer fits beside the operands, so an output tile is 128 rows x NT output reals of
+// one block, computed over K in chunks of 32 reals (16 subcarriers); persistent CTAs take
+// runs of tiles:
+//  * a copy warp brings each raw chunk (128 rows x 16 complex of y_pilot, or of h_ls) by a
+//    2-D TMA box into a 4-stage ring, and the matching chunk of Wr (NT x 32 reals, TF32 hi
+//    then lo, laid out on the host in the canonical K-major layout) by one bulk copy into
+//    one of two W buffers;
+//  * 256 consumer threads apply LS (y conj(p) / |p|^2) and split each value into TF32
+//    hi + lo (both rounded to nearest) in the canonical layout of one of two A buffers;
+//  * one MMA thread issues 4 K-steps x 3 passes (Ah Wh + Ah Wl + Al Wh, M = 128, N = NT,
+//    K = 8) per chunk into one of two FP32 accumulators in tensor memory and commits each
+//    chunk to an mbarrier, which frees that chunk's A and W buffers;
+// and every G_DR chunks the consumers drain the accumulator (TMEM lane = row) into FP32
+// registers while the next group's MMAs run in the other one, storing their row's outputs
+// after a tile's last group.  Only mbarriers order the roles; every wait is bounded.
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "rapro_internal.h"
+#include "rapro_ptx.cuh"
+
+namespace rapro {
+
+namespace {
+
+constexpr int G_ROWS = 128;                     // rows per tile (MMA M, TMEM lanes)
+constexpr int G_KC = 32;                        // input reals per K chunk (16 subcarriers)
+constexpr int G_STAGES = 4;                     // raw-chunk ring depth
+constexpr int G_CONSUMERS = 256;
+constexpr int G_THREADS = G_CONSUMERS + 64;     // + one MMA warp + one copy warp
+constexpr uint32_t G_SBO = (G_KC / 4) * 128;    // 8-row group stride of both operands (bytes)
+constexpr int G_A_PART = G_ROWS * G_KC * 4;     // one TF32 part of an A chunk (bytes)
+constexpr int G_RAW = G_ROWS * (G_KC / 2) * 8;  // one raw chunk (bytes)
+// The tensor cores' FP32 accumulation of one sum loses accuracy linearly in its length, so
+// every G_DR chunks (K = 128 reals) the accumulator is drained into FP32 registers (rounded
+// to nearest) and the next group starts afresh in the other accumulator.
+constexpr int G_DR = 4;
+
+template <int NT>
+__host__ __device__ constexpr uint32_t idesc_tf32() {
+  // D = F32, A = B = TF32, both K-major, M = 128, N = NT.
+  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NT >> 3) << 17) | (uint32_t(G_ROWS >> 4) << 24);
+}
+
+template <int NT>
+__device__ __forceinline__ void mma_tf32_nt(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc_tf32<NT>()), "r"(accumulate ? 1 : 0)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// x rounded to nearest at TF32 (ties away from zero).  Over K = 2B up to thousands of terms a
+// truncating split would leave errors of one sign that add up linearly; rounded hi and lo
+// parts leave unbiased residuals of at most 2^-22 |x|.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__host__ __device__ constexpr int tmem_cols(int nt) { return nt <= 32 ? 32 : nt <= 64 ? 64 : nt <= 128 ? 128 : 256; }
+
+}  // namespace
+
+// NT: output reals per tile (a multiple of 32, at most 128).  LS: the input is y_pilot and
+// LS is applied on load (else the input is h_ls).  Persistent: CTA i takes the contiguous
+// run of output tiles [n_tiles i / grid, n_tiles (i + 1) / grid), tile index = (block, row
+// tile, column tile) with the column tile fastest (the row tile's chunks stay in L2 for the
+// next column tile); the chunks of all its tiles form one stream through the ring, and two
+// accumulators in tensor memory let one tile's read-back overlap the next tile's MMAs.
+template <int NT, bool LS>
+__global__ void __launch_bounds__(G_THREADS, 1)
+    lmmse_tcg_kernel(const __grid_constant__ CUtensorMap map_x, const float2* __restrict__ pil,
+                     float2* __restrict__ out, const unsigned char* __restrict__ w_tiles, int R, int M, int N,
+                     int B, int n_kc, int n_rt, int n_ct, int n_tiles, int w_resident, int* status) {
+  static_assert(NT % 32 == 0 && NT <= 128, "NT: 32-column read-back groups");
+  constexpr int W_PART = NT * G_KC * 4;            // one TF32 part of a W chunk (bytes)
+  constexpr int TCOLS = 2 * tmem_cols(NT);         // two accumulators
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);   // [G_STAGES] raw chunk landed
+  uint64_t* rawfree = full + G_STAGES;                  // [G_STAGES] consumers done with it
+  uint64_t* aready = rawfree + G_STAGES;                // [2] A buffer holds a chunk
+  uint64_t* wfull = aready + 2;                         // [2] W buffer landed
+  uint64_t* done = wfull + 2;                           // [2] MMAs of a chunk finished
+  uint64_t* drained = done + 2;                         // [2] accumulator read back
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 2);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // W: two buffers streaming the column tile's chunks, or (w_resident: one column tile whose
+  // n_kc chunks all fit) every chunk loaded once for the whole run.
+  unsigned char* sA = smem + 1024;                      // [2][hi, lo][G_A_PART]
+  unsigned char* sW = sA + 2 * 2 * G_A_PART;            // [2 or n_kc][hi, lo][W_PART]
+  unsigned char* sRaw = sW + (w_resident ? n_kc : 2) * 2 * W_PART;   // [G_STAGES][G_RAW]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int t_begin = int((long long)n_tiles * blockIdx.x / gridDim.x);
+  const int my_tiles = int((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) - t_begin;
+  const int n_q = my_tiles * n_kc;                      // chunks of the CTA's stream
+  // tile li of this CTA -> (block, first row, column tile)
+  auto tile = [&](int li, int& b, int& r0, int& ct) {
+    const int t = t_begin + li;
+    ct = t % n_ct;
+    const int rest = t / n_ct;
+    r0 = (rest % n_rt) * G_ROWS;
+    b = rest / n_rt;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < G_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&rawfree[s], G_CONSUMERS);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&aready[i], G_CONSUMERS);
+      mbar_init(&wfull[i], 1);
+      mbar_init(&done[i], 1);
+      mbar_init(&drained[i], G_CONSUMERS);
+    }
+    *s_abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(uint32_t(TCOLS))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  auto give_up = [&]() {
+    *s_abort = 1;
+    atomicExch(status, int(RAPRO_ERR_TIMEOUT));
+  };
+
+  if (warp == G_CONSUMERS / 32 + 1) {
+    // ------------------------------------------------ copy warp: raw chunks and W chunks
+    if (lane == 0 && n_q > 0) {
+      prefetch_tensormap(&map_x);
+      int raw_issued = 0, w_issued = 0;
+      bool bad = false;
+      if (w_resident) {                          // column tile 0: all its chunks, once
+        mbar_arrive_expect_tx(&wfull[0], uint32_t(n_kc) * 2 * W_PART);
+        bulk_load(sW, w_tiles, uint32_t(n_kc) * 2 * W_PART, &wfull[0]);
+        w_issued = 1;
+      }
+      for (int q = 0; q < n_q && !bad; ++q) {
+        const int li = q / n_kc, c = q - li * n_kc, s = q % G_STAGES, wb = q & 1;
+        int b, r0, ct;
+        tile(li, b, r0, ct);
+        if (q >= G_STAGES && !mbar_wait_bounded(&rawfree[s], uint32_t(q / G_STAGES - 1) & 1u)) bad = true;
+        if (!bad) {
+          mbar_arrive_expect_tx(&full[s], G_RAW);
+          tma_load_2d(sRaw + s * G_RAW, &map_x, &full[s], b * B + c * (G_KC / 2), r0);
+          ++raw_issued;
+        }
+        // W buffer wb was last read by the MMAs of chunk q - 2
+        if (!w_resident) {
+          if (!bad && q >= 2 && !mbar_wait_bounded(&done[wb], uint32_t((q - 2) >> 1) & 1u)) bad = true;
+          if (!bad) {
+            mbar_arrive_expect_tx(&wfull[wb], 2 * W_PART);
+            bulk_load(sW + wb * 2 * W_PART, w_tiles + (size_t(ct) * n_kc + c) * 2 * W_PART, 2 * W_PART,
+                      &wfull[wb]);
+            ++w_issued;
+          }
+        }
+        if (*s_abort) bad = true;
+      }
+      // Let the copies in flight land before the CTA moves on (all consumed on the normal path).
+      for (int s = 0; s < G_STAGES && s < raw_issued; ++s)
+        (void)mbar_wait_bounded(&full[s], uint32_t((raw_issued - 1 - s) / G_STAGES) & 1u);
+      for (int i = 0; i < 2 && i < w_issued; ++i)
+        (void)mbar_wait_bounded(&wfull[i], uint32_t((w_issued - 1 - i) >> 1) & 1u);
+      if (bad) give_up();
+    }
+  } else if (warp == G_CONSUMERS / 32) {
+    // ------------------------------------------------ MMA warp: one thread issues
+    if (lane == 0 && n_q > 0) {
+      int issued = 0;
+      bool bad = false;
+      const int gpt = (n_kc + G_DR - 1) / G_DR;         // drain groups per tile
+      for (int q = 0; q < n_q; ++q) {
+        const int li = q / n_kc, c = q - li * n_kc, ab = q & 1;
+        const int gg = li * gpt + c / G_DR;             // group of the CTA's stream
+        // accumulator gg & 1 was last drained for group gg - 2
+        if (c % G_DR == 0 && gg >= 2 && !mbar_wait_bounded(&drained[gg & 1], uint32_t((gg - 2) >> 1) & 1u)) {
+          bad = true;
+          break;
+        }
+        const bool w_ok = w_resident ? (q > 0 || mbar_wait_bounded(&wfull[0], 0u))
+                                     : mbar_wait_bounded(&wfull[ab], uint32_t(q >> 1) & 1u);
+        if (!mbar_wait_bounded(&aready[ab], uint32_t(q >> 1) & 1u) || !w_ok || *s_abort) {
+          bad = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned char* ah = sA + ab * 2 * G_A_PART;
+        const unsigned char* al = ah + G_A_PART;
+        const unsigned char* wh = sW + (w_resident ? c : ab) * 2 * W_PART;
+        const unsigned char* wl = wh + W_PART;
+        const uint32_t d = tmem + uint32_t((gg & 1) * tmem_cols(NT));
+#pragma unroll
+        for (int ks = 0; ks < G_KC / 8; ++ks) {
+          const uint64_t dah = smem_desc_kmajor(ah + ks * 256, 128, G_SBO);
+          const uint64_t dwh = smem_desc_kmajor(wh + ks * 256, 128, G_SBO);
+          mma_tf32_nt<NT>(d, dah, dwh, c % G_DR > 0 || ks > 0);
+          mma_tf32_nt<NT>(d, dah, smem_desc_kmajor(wl + ks * 256, 128, G_SBO), true);
+          mma_tf32_nt<NT>(d, smem_desc_kmajor(al + ks * 256, 128, G_SBO), dwh, true);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done[ab]))
+                     : "memory");
+        ++issued;
+      }
+      // The tensor cores finish in order: the last group done means TMEM may be freed.
+      if (issued > 0) (void)mbar_wait_bounded(&done[(issued - 1) & 1], uint32_t((issued - 1) >> 1) & 1u);
+      if (bad) give_up();
+    }
+  } else {
+    // ------------------------------------------------ consumers: LS + split, read-back
+    bool bad = false;
+    // Drain of group gg (tile gg / gpt): warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) and
+    // 32-column groups w / 4 and w / 4 + 2 of accumulator gg & 1 and adds them to its
+    // registers; after a tile's last group the registers (16 complex outputs of the row per
+    // column group) are stored and cleared.  Waits for the MMAs of the group's last chunk,
+    // then frees the accumulator.
+    const int gpt = (n_kc + G_DR - 1) / G_DR;
+    float acc_r[2][32];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
+    auto drain = [&](int gg) -> bool {
+      const int li = gg / gpt, gc = gg - li * gpt;
+      const int ql = li * n_kc + min((gc + 1) * G_DR, n_kc) - 1;
+      if (!mbar_wait_bounded(&done[ql & 1], uint32_t(ql >> 1) & 1u)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int rq = warp & 3;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int g = (warp >> 2) + 2 * i;
+        if (g < NT / 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + (uint32_t(32 * rq) << 16) + uint32_t((gg & 1) * tmem_cols(NT) + 32 * g), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc_r[i][j] += __uint_as_float(v[j]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&drained[gg & 1]);
+      if (gc == gpt - 1) {
+        int b, r0, ct;
+        tile(li, b, r0, ct);
+        const int row = r0 + 32 * rq + lane;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int g = (warp >> 2) + 2 * i;
+          const int j0 = (ct * NT + 32 * g) >> 1;     // first complex output of the group
+          if (g < NT / 32 && row < R) {
+            // pairs of outputs as 16-byte stores (row * N + b * B + j0 is even; so is B)
+            float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (j0 + 2 * j < B) o[j] = make_float4(acc_r[i][4 * j], acc_r[i][4 * j + 1], acc_r[i][4 * j + 2], acc_r[i][4 * j + 3]);
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
+        }
+      }
+      return true;
+    };
+    // Element map of a chunk (128 rows x 8 float4 of two subcarriers): warp w, lane l takes
+    // rows (2w + u) * 8 + (l & 7) and float4 columns c4 = ((l >> 3) + 4h + row) & 7 (u, h in
+    // {0, 1}), so both the raw reads (row stride 128 bytes) and the canonical A writes (core
+    // columns 128 bytes apart) touch eight bank groups per warp.
+    constexpr int NE = (G_ROWS * G_KC / 4) / G_CONSUMERS;   // 4 float4 per thread per chunk
+    auto elem = [&](int k, int& row, int& c4) {
+      row = (2 * warp + (k >> 1)) * 8 + (lane & 7);
+      c4 = ((lane >> 3) + 4 * (k & 1) + row) & 7;
+    };
+    for (int li = 0; li < my_tiles && !bad; ++li) {
+      int b, r0, ct;
+      tile(li, b, r0, ct);
+      // the pilot rows of this thread's two rows of the tile (null past R)
+      const float2* prow[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int rg = r0 + (2 * warp + u) * 8 + (lane & 7);
+        prow[u] = (LS && rg < R) ? pil + size_t(rg / M) * N : nullptr;
+      }
+      for (int c = 0; c < n_kc && !bad; ++c) {
+        const int q = li * n_kc + c, s = q % G_STAGES, ab = q & 1;
+        const int x0 = b * B + c * (G_KC / 2);
+        // the pilots do not depend on the chunk's data: load them before waiting for it
+        float4 pv[NE];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+          int row, c4;
+          elem(k, row, c4);
+          const int sc = x0 + 2 * c4;
+          pv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (LS && prow[k >> 1] && sc + 1 < N) pv[k] = __ldg(reinterpret_cast<const float4*>(prow[k >> 1] + sc));
+        }
+        if (*s_abort || !mbar_wait_bounded(&full[s], uint32_t(q / G_STAGES) & 1u)) {
+          bad = true;
+          break;
+        }
+        // A buffer ab was last read by the MMAs of chunk q - 2
+        if (q >= 2 && !mbar_wait_bounded(&done[ab], uint32_t((q - 2) >> 1) & 1u)) {
+          bad = true;
+          break;
+        }
+        const float4* raw4 = reinterpret_cast<const float4*>(sRaw + s * G_RAW);
+        unsigned char* ah = sA + ab * 2 * G_A_PART;
+        unsigned char* al = ah + G_A_PART;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+          int row, c4;
+          elem(k, row, c4);
+          float4 v = raw4[row * 8 + c4];
+          if (LS) {
+            const int rg = r0 + row, sc = x0 + 2 * c4;
+            const float4 p = pv[k];
+            const float i0 = __fdividef(1.0f, fmaf(p.x, p.x, p.y * p.y));
+            const float i1 = __fdividef(1.0f, fmaf(p.z, p.z, p.w * p.w));
+            // rows past R and subcarriers past n_sc hold zeros (TMA fill): keep them zero
+            v = (rg < R && sc + 1 < N)
+                    ? make_float4(fmaf(v.x, p.x, v.y * p.y) * i0, fmaf(v.y, p.x, -v.x * p.y) * i0,
+                                  fmaf(v.z, p.z, v.w * p.w) * i1, fmaf(v.w, p.z, -v.z * p.w) * i1)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+          const int off = (row >> 3) * int(G_SBO) + c4 * 128 + (row & 7) * 16;
+          *reinterpret_cast<float4*>(ah + off) = h;
+          *reinterpret_cast<float4*>(al + off) = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y),
+                                                             tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
+        }
+        fence_proxy_async_shared();              // the MMAs read what was written here
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&aready[ab]);
+        mbar_arrive(&rawfree[s]);
+        // the first chunk of group gg is handed over: drain the previous group meanwhile
+        const int gg = li * gpt + c / G_DR;
+        if (c % G_DR == 0 && gg >= 1 && !drain(gg - 1)) bad = true;
+      }
+    }
+    if (!bad && my_tiles > 0 && !drain(my_tiles * gpt - 1)) bad = true;
+    if (bad) give_up();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TCOLS))
+                 : "memory");
+}
+
+// ------------------------------------------------------------------------------ host
+static int tcg_nt(int B) { return 2 * B <= 96 ? 96 : 128; }
+
+template <int NT>
+static size_t tcg_smem_bytes(int w_chunks) {
+  return 1024 + 2 * 2 * size_t(G_A_PART) + size_t(w_chunks) * 2 * NT * G_KC * 4 + size_t(G_STAGES) * G_RAW;
+}
+
+constexpr size_t kTcgSmemMax = 232448;   // 227 KB, the per-CTA limit
+
+static float tf32_round_host(float x) {
+  // Round to nearest (ties away) at 10 explicit mantissa bits.
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u = (u + 0x1000u) & 0xffffe000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// Blocks up to 2048 subcarriers (W tiles of up to 128 MB).  The drained accumulation keeps
+// the error at that of a K = 128 sum (measured at n_sc = 1200, B = 1200: 1.6e-5 relative
+// with one accumulator over all of K = 2400, against the 1e-5 bar).
+constexpr int kTcgMaxBlock = 2048;
+
+bool lmmse_tcg_shape_ok(const Plan& pl) {
+  const long long rows = (long long)pl.T * pl.p.K * pl.p.M;
+  return !pl.comb && pl.p.precision == RAPRO_PREC_FP32 && pl.B > 16 && pl.B <= kTcgMaxBlock && pl.B % 2 == 0 &&
+         pl.tail == 0 && rows < (1ll << 31) && pl.p.n_sc / pl.B <= 65535;
+}
+
+// Wr (2B x 2B reals) cut into tiles of NT output reals x chunks of 32 input reals, each
+// chunk TF32 hi then lo in the canonical K-major layout, tiles one after the other.
+void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out) {
+  const int B = pl.B, NT = tcg_nt(B), K2 = 2 * B;
+  const int n_nt = (K2 + NT - 1) / NT, n_kc = (K2 + G_KC - 1) / G_KC;
+  const size_t part = size_t(NT) * G_KC * 4;
+  out.assign(size_t(n_nt) * n_kc * 2 * part, 0);
+  for (int t = 0; t < n_nt; ++t)
+    for (int c = 0; c < n_kc; ++c) {
+      unsigned char* base = out.data() + (size_t(t) * n_kc + c) * 2 * part;
+      for (int nn = 0; nn < NT; ++nn)
+        for (int kk = 0; kk < G_KC; ++kk) {
+          const int n = t * NT + nn, k = c * G_KC + kk;
+          if (n >= K2 || k >= K2) continue;
+          const float2 w = pl.w_main[size_t(n >> 1) * B + (k >> 1)];
+          const float vals[2][2] = {{w.x, -w.y}, {w.y, w.x}};   // [out re/im][in re/im]
+          const float f = vals[n & 1][k & 1];
+          const float h = tf32_round_host(f), l = tf32_round_host(f - h);
+          const size_t off = size_t((nn >> 3) * G_SBO + (kk >> 2) * 128 + (nn & 7) * 16 + (kk & 3) * 4);
+          std::memcpy(base + off, &h, 4);
+          std::memcpy(base + part + off, &l, 4);
+        }
+    }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tcg_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool lmmse_tcg_ok(const Plan& pl, const float2* x, const float2* out) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(out);
+  return pl.d_w_tcg != nullptr && (a & 15) == 0 && lmmse_tcg_shape_ok(pl) && tcg_encode() != nullptr;
+}
+
+template <int NT>
+static cudaError_t launch_tcg_nt(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st) {
+  const int B = pl.B, N = pl.p.n_sc, M = pl.p.M, R = pl.T * pl.p.K * pl.p.M;
+  const int n_nt = (2 * B + NT - 1) / NT, n_kc = (2 * B + G_KC - 1) / G_KC;
+  // 2-D map over x [R][N] complex64 with boxes of 16 subcarriers x 128 rows.
+  CUtensorMap map;
+  cuuint64_t dims[2] = {cuuint64_t(N), cuuint64_t(R)};
+  cuuint64_t strides[1] = {cuuint64_t(N) * 8};
+  cuuint32_t box[2] = {cuuint32_t(G_KC / 2), cuuint32_t(G_ROWS)};
+  cuuint32_t es[2] = {1, 1};
+  if (tcg_encode()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<float2*>(x), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const int n_rt = (R + G_ROWS - 1) / G_ROWS;
+  const long long tiles = (long long)n_rt * n_nt * (N / B);
+  if (tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = int(tiles), grid = std::min(n_tiles, sms);   // one CTA per SM (shared memory)
+  const int w_resident = n_nt == 1 && n_kc > 2 && tcg_smem_bytes<NT>(n_kc) <= kTcgSmemMax ? 1 : 0;
+  const size_t smem = tcg_smem_bytes<NT>(w_resident ? n_kc : 2);
+  const unsigned char* w = static_cast<const unsigned char*>(pl.d_w_tcg);
+  if (pil)
+    lmmse_tcg_kernel<NT, true><<<grid, G_THREADS, smem, st>>>(map, pil, out, w, R, M, N, B, n_kc, n_rt, n_nt,
+                                                              n_tiles, w_resident, pl.d_status);
+  else
+    lmmse_tcg_kernel<NT, false><<<grid, G_THREADS, smem, st>>>(map, pil, out, w, R, M, N, B, n_kc, n_rt, n_nt,
+                                                               n_tiles, w_resident, pl.d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st) {
+  return tcg_nt(pl.B) == 96 ? launch_tcg_nt<96>(pl, x, pil, out, st) : launch_tcg_nt<128>(pl, x, pil, out, st);
+}
+
+cudaError_t prepare_lmmse_tcg(int device) {
+  static std::once_flag flags[64];
+  static cudaError_t result[64];
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  std::call_once(flags[device], [device] {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true>, A, int(kTcgSmemMax));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, false>, A, int(kTcgSmemMax));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true>, A, int(kTcgSmemMax));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, false>, A, int(kTcgSmemMax));
+    result[device] = e;
+  });
+  return result[device];
+}
+
+}  // namespace rapro

@@ -187,7 +187,7 @@ rapro_status rapro_plan_tune(rapro_plan* plan, const rapro_c32* y_pilot, const r
 rapro_status rapro_plan_set_variant(rapro_plan* plan, int est_variant, int det_split, int est_ctas_per_sm) {
   if (!plan) return bad("plan is NULL");
   Plan* pl = reinterpret_cast<Plan*>(plan);
-  if (est_variant < -1 || est_variant >= EST_VARIANTS) return bad("est_variant must be -1 .. 3");
+  if (est_variant < -1 || est_variant >= EST_VARIANTS) return bad("est_variant must be -1 .. 4");
   if (pl->comb && est_variant != -1) return bad("comb plans have one estimator (est_variant -1)");
   const int max_split = make_det_tiles(pl->p.K, pl->D).msplit;
   if (det_split < 1 || det_split > max_split) return bad("det_split out of range for this plan");

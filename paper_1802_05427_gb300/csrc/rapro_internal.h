@@ -48,6 +48,7 @@ struct Plan {
   float2* d_h_work = nullptr;      // [T][K][M][n_sc] estimate workspace
   int* d_status = nullptr;         // device status word
   void* d_w_tc = nullptr;          // tensor-core filter operand (canonical layout), or null
+  void* d_w_tcg = nullptr;         // large-B tensor-core GEMM operand (tiles of Wr chunks), or null
   int est_variant = -1;            // estimator kernel (EST_*), -1 = built-in choice; set by rapro_plan_tune
   int recv_form = RAPRO_RECV_SPLIT; // rapro_receive_form of rapro_receive_subframe
   // Tensor-core estimator CTAs per SM (0: as many as fit).  One leaves each SM room for a
@@ -113,7 +114,7 @@ constexpr float kFp64CondLimit = 1.0e6f;
 cudaError_t prepare_estimate(int device);
 cudaError_t prepare_lmmse_tc(int device);
 // Estimator kernels a plan can use (the autotuner times the ones that apply).
-enum { EST_TC = 0, EST_STREAM = 1, EST_SMALL = 2, EST_TILED = 3, EST_VARIANTS = 4 };
+enum { EST_TC = 0, EST_STREAM = 1, EST_SMALL = 2, EST_TILED = 3, EST_TCG = 4, EST_VARIANTS = 5 };
 bool lmmse_variant_ok(const Plan& pl, int v, const float2* x, const float2* pil, const float2* out);
 // Detector warps per role of a plan by default: one, so that a detector CTA and an estimator
 // CTA of another subframe in flight share an SM (registers allow it only then).
@@ -125,6 +126,13 @@ bool lmmse_tc_shape_ok(const Plan& pl);
 void build_lmmse_tc_weights(const Plan& pl, std::vector<unsigned char>& out);
 bool lmmse_tc_ok(const Plan& pl, const float2* y, const float2* pil, const float2* out);
 cudaError_t launch_lmmse_tc(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st);
+// Tensor-core GEMM form for larger blocks (even 16 < B <= 2048 dividing n_sc, FP32 plans,
+// aligned arrays); pil may be null (the input is then h_ls).
+bool lmmse_tcg_shape_ok(const Plan& pl);
+void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out);
+bool lmmse_tcg_ok(const Plan& pl, const float2* x, const float2* out);
+cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st);
+cudaError_t prepare_lmmse_tcg(int device);
 
 cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
                           unsigned char* labels, float* llr, int* info, cudaStream_t st);

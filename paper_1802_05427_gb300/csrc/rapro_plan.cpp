@@ -446,12 +446,13 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if ((e = prepare_detect(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "detector set-up"); }
   if ((e = prepare_estimate(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "estimator set-up"); }
   if ((e = prepare_lmmse_tc(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core estimator set-up"); }
+  if ((e = prepare_lmmse_tcg(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core GEMM set-up"); }
   if ((e = prepare_comb(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "comb estimator set-up"); }
   if ((e = prepare_adjoint(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "adjoint set-up"); }
   const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
-    cudaFree(pl->d_w_tc); cudaFree(pl->d_w_comb); cudaFree(pl->d_fix);
+    cudaFree(pl->d_w_tc); cudaFree(pl->d_w_tcg); cudaFree(pl->d_w_comb); cudaFree(pl->d_fix);
     delete pl;
     return cuda_fail(err, what);
   };
@@ -484,6 +485,13 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
     if ((e = cudaMemcpy(pl->d_w_tc, wtc.data(), wtc.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(e, "cudaMemcpy W (tensor cores)");
   }
+  if (lmmse_tcg_shape_ok(*pl)) {
+    std::vector<unsigned char> wtg;
+    build_lmmse_tcg_weights(*pl, wtg);
+    if ((e = cudaMalloc(&pl->d_w_tcg, wtg.size())) != cudaSuccess) return fail(e, "cudaMalloc W (tensor-core GEMM)");
+    if ((e = cudaMemcpy(pl->d_w_tcg, wtg.data(), wtg.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(e, "cudaMemcpy W (tensor-core GEMM)");
+  }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan upload");
   *out = reinterpret_cast<rapro_plan*>(pl);
   return RAPRO_OK;
@@ -498,6 +506,7 @@ rapro_status rapro_plan_destroy(rapro_plan* plan) {
   cudaFree(pl->d_h_work);
   cudaFree(pl->d_status);
   cudaFree(pl->d_w_tc);
+  cudaFree(pl->d_w_tcg);
   cudaFree(pl->d_w_comb);
   cudaFree(pl->d_fix);
   delete pl;

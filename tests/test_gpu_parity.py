@@ -173,6 +173,46 @@ LS_LMMSE_CASES = [
 ]
 
 
+TCG_CASES = [
+    # M, K, N, n_fft, B: even B > 16 dividing N (the tensor-core GEMM); rows not a multiple
+    # of the 128-row tile, K chunks of 16 subcarriers running past the block (B = 18, 100),
+    # one block (the full LMMSE, B = N), several output tiles (2B > 128)
+    (20, 3, 72, 128, 18), (50, 5, 96, 256, 24), (7, 2, 96, 128, 48), (16, 2, 200, 256, 100),
+    (9, 1, 120, 256, 120), (33, 4, 240, 512, 80),
+]
+
+
+@pytest.mark.parametrize("case", TCG_CASES)
+def test_tensor_core_gemm_estimator_parity(case):
+    """The large-block filter on tcgen05 (three TF32 passes), with LS fused (rapro_ce_ls_lmmse)
+    and on a given h_ls (rapro_ce_lmmse_subblock), against the oracle; the built-in choice and
+    the explicit variant agree, and the FP32 tiled kernel agrees with both."""
+    M, K, N, nfft, B = case
+    sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, snr_db=12.0, qam_bits=2)
+    sf, c64 = _inputs(sh, 31)
+    h_ls = O.ls_estimate(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128))
+    ref = O.subblock_lmmse(h_ls, B, oracle_r(sh), sh.sigma2)
+    plan = R.Plan(params_for(sh, B))
+    shp = plan.shapes()["h"]
+    yp, pil, hl = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(synth.as_c64(h_ls))
+    outs = {}
+    for ev in (-1, 4, 3):
+        R.rapro_plan_set_variant(plan, ev, 1, 1)
+        for fused in (True, False):
+            h = torch.full(shp, 5.0 + 5j, dtype=torch.complex64, device="cuda")
+            if fused:
+                R.rapro_ce_ls_lmmse(plan, yp, pil, h)
+            else:
+                R.rapro_ce_lmmse_subblock(plan, hl, h)
+            g = _host(h)
+            e = rel_err_per(g, ref, axes=(2, 3))
+            assert e.max() <= TOL, (ev, fused, e.max())
+            outs[(ev, fused)] = g
+    assert np.array_equal(outs[(-1, True)], outs[(4, True)])           # the built-in choice is the GEMM
+    assert plan.device_status() == 0
+    plan.close()
+
+
 @pytest.mark.parametrize("case", LS_LMMSE_CASES)
 def test_ls_lmmse_parity(case):
     """LS (Eq. 9) and the sub-block filter (Eq. 12, 17) in one call, against both oracle steps."""
@@ -753,9 +793,9 @@ def test_autotuner_picks_an_applicable_kernel_and_keeps_parity(case):
     assert R.rapro_plan_variant(plan)[0] == -1
     R.rapro_plan_tune(plan, yp, pil, yd, h, x)
     ev, split, grid = R.rapro_plan_variant(plan)
-    assert ev in (0, 1, 2, 3) and split in (1, 2) and grid in (0, 1)
+    assert ev in (0, 1, 2, 3, 4) and split in (1, 2) and grid in (0, 1)
     if B > 32:
-        assert ev == 3
+        assert ev in (3, 4)                 # tiled FP32 or the tensor-core GEMM
     if B > 16:
         assert not R.rapro_receive_is_fused(plan, yp, yd)   # the fused form does not apply
     lab = torch.empty(s["labels"], dtype=torch.uint8, device="cuda")
@@ -778,7 +818,7 @@ def test_every_kernel_choice_keeps_parity(case):
     s = plan.shapes()
     assert R.rapro_plan_variant(plan) == (-1, 1, 1)                  # the throughput defaults
     yp, pil, yd = _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"])
-    for ev in (-1, 0, 1, 2, 3):
+    for ev in (-1, 0, 1, 2, 3, 4):
         for split in (1, 2):
             for grid in (0, 1):
                 R.rapro_plan_set_variant(plan, ev, split, grid)
@@ -790,10 +830,10 @@ def test_every_kernel_choice_keeps_parity(case):
                 R.rapro_receive_subframe(plan, yp, pil, yd, x, lab, llr, h_out=h)
                 assert rel_err_per(_host(h), o["h"], axes=(2, 3)).max() <= TOL, (ev, split, grid)
                 check_detection(dict(x_eq=_host(x), labels=_host(lab), llr=_host(llr)), o, sh.qam_bits)
-    for bad in ((4, 1, 1), (-2, 1, 1), (-1, 0, 1), (-1, 3, 1), (-1, 1, 9), (-1, 1, -1)):
+    for bad in ((5, 1, 1), (-2, 1, 1), (-1, 0, 1), (-1, 3, 1), (-1, 1, 9), (-1, 1, -1)):
         with pytest.raises(R.RaproError):
             R.rapro_plan_set_variant(plan, *bad)
-    assert R.rapro_plan_variant(plan) == (3, 2, 1)                   # a bad call changes nothing
+    assert R.rapro_plan_variant(plan) == (4, 2, 1)                   # a bad call changes nothing
     assert plan.device_status() == 0
     plan.close()
 
