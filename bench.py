@@ -585,8 +585,12 @@ def run_rapro(args):
     # stream gets a plan of its own.
     prec = {}
     if want("precision") and rank == 0 and world == 1 and B % 2 == 0 and B <= 16 and sh.n_sc % B == 0:
-        for name, pv in (("bf16_tc", R.RAPRO_PREC_BF16), ("fp16_tc", R.RAPRO_PREC_FP16)):
-            pb = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B, sigma2=sh.sigma2,
+        forms = [("bf16_tc", R.RAPRO_PREC_BF16, B), ("fp16_tc", R.RAPRO_PREC_FP16, B)]
+        if want("sweep"):                  # the sub-block sweep of the precision forms
+            forms += [(f"{n}_B{Bs}", pv, Bs) for Bs in (48, 100, 1200)
+                      for n, pv in (("bf16_tc", R.RAPRO_PREC_BF16), ("fp16_tc", R.RAPRO_PREC_FP16))]
+        for name, pv, Bp in forms:
+            pb = R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=Bp, sigma2=sh.sigma2,
                                qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms, precision=pv)
             plbs = [R.Plan(pb) for _ in range(IN_FLIGHT)]
 
@@ -618,9 +622,11 @@ def run_rapro(args):
                             st.wait_event(join)
                 torch.cuda.synchronize()
                 gb.append(g)
-            us_b_full, us_b_est = time_graph(gb[0], 64), time_graph(gb[1], 64)
-            prec[name] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est,
-                          "estimator_hbm_frac": alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)}
+            reps_b = 64 if Bp < 1200 else 4
+            us_b_full, us_b_est = time_graph(gb[0], reps_b), time_graph(gb[1], reps_b)
+            prec[name] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est}
+            if Bp == B:
+                prec[name]["estimator_hbm_frac"] = alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)
             for plb in plbs:
                 assert plb.device_status() == 0
                 plb.close()

@@ -105,7 +105,7 @@ typedef enum {
   RAPRO_PREC_FP32 = 0,
   /* Precision form: one BF16 pass on the tensor cores, FP32 accumulation (W and the LS
    * estimate rounded to BF16; relative filter error ~ 2^-8).  Needs the orthogonal layout,
-   * an even B <= 16 dividing n_sc and 16-byte aligned arrays; rapro_ce_lmmse_subblock and
+   * an even B <= 2048 dividing n_sc and 16-byte aligned arrays; rapro_ce_lmmse_subblock and
    * w_override are not available (RAPRO_ERR_UNSUPPORTED).  The detector of such a plan
    * falls back to FP64 for every subcarrier whose FP32 Cholesky pivots give
    * (max L_jj / min L_jj)^2 > 1e6 (a lower bound of cond(A)) or fail: Eq. 22 solved again

@@ -434,7 +434,8 @@ cudaError_t launch_lmmse(const Plan& pl, const float2* x, const float2* pil,
 }
 
 bool lmmse_variant_ok(const Plan& pl, int v, const float2* x, const float2* pil, const float2* out) {
-  if (half_precision(pl.p)) return v == EST_TC && lmmse_tc_ok(pl, x, pil, out);
+  if (half_precision(pl.p))
+    return (v == EST_TC && lmmse_tc_ok(pl, x, pil, out)) || (v == EST_TCG && pil && lmmse_tcg_ok(pl, x, out));
   switch (v) {
     case EST_TC: return lmmse_tc_ok(pl, x, pil, out);
     case EST_STREAM: return pil && pl.B <= LMMSE_SMALL_MAX && stream_ok(x, pil, out, pl.p.n_sc, pl.B, pl.nb);
@@ -451,7 +452,8 @@ cudaError_t launch_lmmse_variant(const Plan& pl, int v, const float2* x, const f
                                  cudaStream_t st) {
   if (v < 0 || !lmmse_variant_ok(pl, v, x, pil, out)) {
     if (lmmse_tc_ok(pl, x, pil, out)) return launch_lmmse_tc(pl, x, pil, out, st);
-    if (half_precision(pl.p)) return cudaErrorNotSupported;   // never a silent FP32 fallback
+    if (half_precision(pl.p))   // the 16-bit forms run on the tensor cores or not at all
+      return pil && lmmse_tcg_ok(pl, x, out) ? launch_lmmse_tcg(pl, x, pil, out, st) : cudaErrorNotSupported;
     if (lmmse_tcg_ok(pl, x, out)) return launch_lmmse_tcg(pl, x, pil, out, st);
     v = pl.B <= LMMSE_SMALL_MAX ? EST_STREAM : EST_TILED;
   }

@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "host_round.h"
 #include "rapro_internal.h"
 #include "rapro_ptx.cuh"
 
@@ -73,13 +74,8 @@ __device__ __forceinline__ void mma_f16kind(uint32_t d_tmem, uint64_t a, uint64_
 // Two floats rounded to nearest even into one 32-bit word, the first at the lower address.
 template <int OP>
 __device__ __forceinline__ uint32_t pack16x2(float lo, float hi) {
-  if constexpr (OP == OP_FP16) {
-    const __half2 v = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&v);
-  } else {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&v);
-  }
+  if constexpr (OP == OP_FP16) return pack_f16x2(lo, hi);
+  else return pack_bf16x2(lo, hi);
 }
 
 }  // namespace
@@ -381,43 +377,6 @@ static size_t tc_smem_bytes(int B) {
          size_t(TC_STAGES) * TC_ROWS * B * sizeof(float2);
 }
 
-static float tf32_host(float x) {
-  // Round to nearest (ties away) at 10 explicit mantissa bits, as cvt.rna.tf32.f32.
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  if ((u & 0x7f800000u) == 0x7f800000u) return x;
-  u = (u + 0x1000u) & 0xffffe000u;
-  float r;
-  std::memcpy(&r, &u, 4);
-  return r;
-}
-
-// Round to nearest even at FP16 (10 explicit mantissa bits, subnormals below 2^-14,
-// overflow to infinity).
-static uint16_t f16_host(float x) {
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  const uint32_t sign = (u >> 16) & 0x8000u, a = u & 0x7fffffffu;
-  if (a > 0x7f800000u) return uint16_t(sign | 0x7e00u);               // NaN
-  if (a >= 0x47800000u) return uint16_t(sign | 0x7c00u);              // |x| >= 65536: inf
-  if (a < 0x38800000u) {                                               // |x| < 2^-14
-    float f;
-    std::memcpy(&f, &a, 4);
-    return uint16_t(sign | uint32_t(std::nearbyint(f * 16777216.0f)));   // units of 2^-24, ties even
-  }
-  uint32_t h = (a - 0x38000000u) >> 13;                                // rebias 127 -> 15
-  const uint32_t rem = a & 0x1fffu;
-  if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;              // may carry into the exponent
-  return uint16_t(sign | (h >= 0x7c00u ? 0x7c00u : h));
-}
-
-static uint16_t bf16_host(float x) {
-  // Round to nearest even at 7 explicit mantissa bits (finite inputs).
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  u += 0x7fffu + ((u >> 16) & 1u);
-  return uint16_t(u >> 16);
-}
 
 // Reals per row-block: 2B padded to the K step (8 for TF32, 16 for BF16).
 static int kr_for(int B, bool half) { return half ? (2 * B + 15) / 16 * 16 : (2 * B + 7) / 8 * 8; }
@@ -470,10 +429,10 @@ void build_lmmse_tc_weights(const Plan& pl, std::vector<unsigned char>& out) {
           const size_t off = size_t((n / 8) * SBO + (k / ce) * 128 + (n % 8) * 16 + (k % ce) * elt);
           const float f = vals[a][c];
           if (bf) {
-            const uint16_t h = f16 ? f16_host(f) : bf16_host(f);
+            const uint16_t h = f16 ? f16_round_host(f) : bf16_round_host(f);
             std::memcpy(&out[off], &h, 2);
           } else {
-            const float h = tf32_host(f), l = tf32_host(f - h);
+            const float h = tf32_round_host(f), l = tf32_round_host(f - h);
             std::memcpy(&out[off], &h, 4);
             std::memcpy(&out[part + off], &l, 4);
           }

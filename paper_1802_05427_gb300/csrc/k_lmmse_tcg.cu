@@ -28,6 +28,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "host_round.h"
 #include "rapro_internal.h"
 #include "rapro_ptx.cuh"
 
@@ -40,27 +41,43 @@ constexpr int G_KC = 32;                        // input reals per K chunk (16 s
 constexpr int G_STAGES = 4;                     // raw-chunk ring depth
 constexpr int G_CONSUMERS = 256;
 constexpr int G_THREADS = G_CONSUMERS + 64;     // + one MMA warp + one copy warp
-constexpr uint32_t G_SBO = (G_KC / 4) * 128;    // 8-row group stride of both operands (bytes)
-constexpr int G_A_PART = G_ROWS * G_KC * 4;     // one TF32 part of an A chunk (bytes)
+// Operand forms: three TF32 passes (FP32 accuracy) or one pass of BF16 / FP16 operands.
+enum { G_TF32X3 = 0, G_BF16 = 1, G_FP16 = 2 };
+__host__ __device__ constexpr int g_elt(int op) { return op == G_TF32X3 ? 4 : 2; }
+// 8-row group stride of both operands (a chunk row is 32 reals = 32 * elt bytes)
+__host__ __device__ constexpr uint32_t g_sbo(int op) { return uint32_t(G_KC * g_elt(op) / 16) * 128; }
+__host__ __device__ constexpr int g_parts(int op) { return op == G_TF32X3 ? 2 : 1; }   // hi, lo / one
+__host__ __device__ constexpr int g_a_part(int op) { return G_ROWS * G_KC * g_elt(op); }
 constexpr int G_RAW = G_ROWS * (G_KC / 2) * 8;  // one raw chunk (bytes)
 // The tensor cores' FP32 accumulation of one sum loses accuracy linearly in its length, so
 // every G_DR chunks (K = 128 reals) the accumulator is drained into FP32 registers (rounded
 // to nearest) and the next group starts afresh in the other accumulator.
 constexpr int G_DR = 4;
 
-template <int NT>
-__host__ __device__ constexpr uint32_t idesc_tf32() {
-  // D = F32, A = B = TF32, both K-major, M = 128, N = NT.
-  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NT >> 3) << 17) | (uint32_t(G_ROWS >> 4) << 24);
+template <int NT, int OP>
+__host__ __device__ constexpr uint32_t idesc_g() {
+  // D = F32; A = B = TF32 (format 2 of kind::tf32) or BF16 (1) / FP16 (0) of kind::f16;
+  // both K-major, M = 128, N = NT.
+  return (1u << 4) | (uint32_t(OP == G_TF32X3 ? 2 : OP == G_BF16 ? 1 : 0) << 7) |
+         (uint32_t(OP == G_TF32X3 ? 2 : OP == G_BF16 ? 1 : 0) << 10) | (uint32_t(NT >> 3) << 17) |
+         (uint32_t(G_ROWS >> 4) << 24);
 }
 
-template <int NT>
-__device__ __forceinline__ void mma_tf32_nt(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc_tf32<NT>()), "r"(accumulate ? 1 : 0)
-      : "memory");
+// One K step (8 TF32 or 16 BF16 / FP16 values, 32 bytes of each row).
+template <int NT, int OP>
+__device__ __forceinline__ void mma_g(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
+  if constexpr (OP == G_TF32X3)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_g<NT, OP>()), "r"(accumulate ? 1 : 0)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_g<NT, OP>()), "r"(accumulate ? 1 : 0)
+        : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -85,18 +102,22 @@ __host__ __device__ constexpr int tmem_cols(int nt) { return nt <= 32 ? 32 : nt 
 }  // namespace
 
 // NT: output reals per tile (a multiple of 32, at most 128).  LS: the input is y_pilot and
-// LS is applied on load (else the input is h_ls).  Persistent: CTA i takes the contiguous
+// LS is applied on load (else the input is h_ls).  OP: operand form (G_TF32X3, G_BF16,
+// G_FP16; the 16-bit forms are one pass with no lo parts).  Persistent: CTA i takes the contiguous
 // run of output tiles [n_tiles i / grid, n_tiles (i + 1) / grid), tile index = (block, row
 // tile, column tile) with the column tile fastest (the row tile's chunks stay in L2 for the
 // next column tile); the chunks of all its tiles form one stream through the ring, and two
 // accumulators in tensor memory let one tile's read-back overlap the next tile's MMAs.
-template <int NT, bool LS>
+template <int NT, bool LS, int OP>
 __global__ void __launch_bounds__(G_THREADS, 1)
     lmmse_tcg_kernel(const __grid_constant__ CUtensorMap map_x, const float2* __restrict__ pil,
                      float2* __restrict__ out, const unsigned char* __restrict__ w_tiles, int R, int M, int N,
                      int B, int n_kc, int n_rt, int n_ct, int n_tiles, int w_resident, int* status) {
   static_assert(NT % 32 == 0 && NT <= 128, "NT: 32-column read-back groups");
-  constexpr int W_PART = NT * G_KC * 4;            // one TF32 part of a W chunk (bytes)
+  constexpr int ELT = g_elt(OP), NP = g_parts(OP), G_A_PART = g_a_part(OP);
+  constexpr uint32_t G_SBO = g_sbo(OP);
+  constexpr int W_PART = NT * G_KC * ELT;          // one part of a W chunk (bytes)
+  constexpr int KSTEPS = G_KC * ELT / 32;          // MMAs per chunk and pass (32 bytes of K each)
   constexpr int TCOLS = 2 * tmem_cols(NT);         // two accumulators
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);   // [G_STAGES] raw chunk landed
@@ -109,9 +130,9 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   // W: two buffers streaming the column tile's chunks, or (w_resident: one column tile whose
   // n_kc chunks all fit) every chunk loaded once for the whole run.
-  unsigned char* sA = smem + 1024;                      // [2][hi, lo][G_A_PART]
-  unsigned char* sW = sA + 2 * 2 * G_A_PART;            // [2 or n_kc][hi, lo][W_PART]
-  unsigned char* sRaw = sW + (w_resident ? n_kc : 2) * 2 * W_PART;   // [G_STAGES][G_RAW]
+  unsigned char* sA = smem + 1024;                      // [2][NP][G_A_PART]
+  unsigned char* sW = sA + 2 * NP * G_A_PART;           // [2 or n_kc][NP][W_PART]
+  unsigned char* sRaw = sW + (w_resident ? n_kc : 2) * NP * W_PART;   // [G_STAGES][G_RAW]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int t_begin = int((long long)n_tiles * blockIdx.x / gridDim.x);
   const int my_tiles = int((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) - t_begin;
@@ -161,8 +182,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
       int raw_issued = 0, w_issued = 0;
       bool bad = false;
       if (w_resident) {                          // column tile 0: all its chunks, once
-        mbar_arrive_expect_tx(&wfull[0], uint32_t(n_kc) * 2 * W_PART);
-        bulk_load(sW, w_tiles, uint32_t(n_kc) * 2 * W_PART, &wfull[0]);
+        mbar_arrive_expect_tx(&wfull[0], uint32_t(n_kc) * NP * W_PART);
+        bulk_load(sW, w_tiles, uint32_t(n_kc) * NP * W_PART, &wfull[0]);
         w_issued = 1;
       }
       for (int q = 0; q < n_q && !bad; ++q) {
@@ -179,8 +200,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         if (!w_resident) {
           if (!bad && q >= 2 && !mbar_wait_bounded(&done[wb], uint32_t((q - 2) >> 1) & 1u)) bad = true;
           if (!bad) {
-            mbar_arrive_expect_tx(&wfull[wb], 2 * W_PART);
-            bulk_load(sW + wb * 2 * W_PART, w_tiles + (size_t(ct) * n_kc + c) * 2 * W_PART, 2 * W_PART,
+            mbar_arrive_expect_tx(&wfull[wb], NP * W_PART);
+            bulk_load(sW + wb * NP * W_PART, w_tiles + (size_t(ct) * n_kc + c) * NP * W_PART, NP * W_PART,
                       &wfull[wb]);
             ++w_issued;
           }
@@ -215,18 +236,20 @@ __global__ void __launch_bounds__(G_THREADS, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned char* ah = sA + ab * 2 * G_A_PART;
-        const unsigned char* al = ah + G_A_PART;
-        const unsigned char* wh = sW + (w_resident ? c : ab) * 2 * W_PART;
-        const unsigned char* wl = wh + W_PART;
+        const unsigned char* ah = sA + ab * NP * G_A_PART;
+        const unsigned char* al = ah + G_A_PART;         // TF32 only
+        const unsigned char* wh = sW + (w_resident ? c : ab) * NP * W_PART;
+        const unsigned char* wl = wh + W_PART;           // TF32 only
         const uint32_t d = tmem + uint32_t((gg & 1) * tmem_cols(NT));
 #pragma unroll
-        for (int ks = 0; ks < G_KC / 8; ++ks) {
+        for (int ks = 0; ks < KSTEPS; ++ks) {
           const uint64_t dah = smem_desc_kmajor(ah + ks * 256, 128, G_SBO);
           const uint64_t dwh = smem_desc_kmajor(wh + ks * 256, 128, G_SBO);
-          mma_tf32_nt<NT>(d, dah, dwh, c % G_DR > 0 || ks > 0);
-          mma_tf32_nt<NT>(d, dah, smem_desc_kmajor(wl + ks * 256, 128, G_SBO), true);
-          mma_tf32_nt<NT>(d, smem_desc_kmajor(al + ks * 256, 128, G_SBO), dwh, true);
+          mma_g<NT, OP>(d, dah, dwh, c % G_DR > 0 || ks > 0);
+          if constexpr (OP == G_TF32X3) {
+            mma_g<NT, OP>(d, dah, smem_desc_kmajor(wl + ks * 256, 128, G_SBO), true);
+            mma_g<NT, OP>(d, smem_desc_kmajor(al + ks * 256, 128, G_SBO), dwh, true);
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&done[ab]))
@@ -332,7 +355,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
           break;
         }
         const float4* raw4 = reinterpret_cast<const float4*>(sRaw + s * G_RAW);
-        unsigned char* ah = sA + ab * 2 * G_A_PART;
+        unsigned char* ah = sA + ab * NP * G_A_PART;
         unsigned char* al = ah + G_A_PART;
 #pragma unroll
         for (int k = 0; k < NE; ++k) {
@@ -350,11 +373,19 @@ __global__ void __launch_bounds__(G_THREADS, 1)
                                   fmaf(v.z, p.z, v.w * p.w) * i1, fmaf(v.w, p.z, -v.z * p.w) * i1)
                     : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-          const int off = (row >> 3) * int(G_SBO) + c4 * 128 + (row & 7) * 16;
-          *reinterpret_cast<float4*>(ah + off) = h;
-          *reinterpret_cast<float4*>(al + off) = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y),
-                                                             tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
+          if constexpr (OP == G_TF32X3) {
+            const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+            const int off = (row >> 3) * int(G_SBO) + c4 * 128 + (row & 7) * 16;
+            *reinterpret_cast<float4*>(ah + off) = h;
+            *reinterpret_cast<float4*>(al + off) = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y),
+                                                               tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
+          } else {
+            // four 16-bit reals: half of a 16-byte core row (eight reals)
+            const int off = (row >> 3) * int(G_SBO) + (c4 >> 1) * 128 + (row & 7) * 16 + (c4 & 1) * 8;
+            *reinterpret_cast<uint2*>(ah + off) =
+                OP == G_FP16 ? make_uint2(pack_f16x2(v.x, v.y), pack_f16x2(v.z, v.w))
+                             : make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+          }
         }
         fence_proxy_async_shared();              // the MMAs read what was written here
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -378,23 +409,18 @@ __global__ void __launch_bounds__(G_THREADS, 1)
 // ------------------------------------------------------------------------------ host
 static int tcg_nt(int B) { return 2 * B <= 96 ? 96 : 128; }
 
-template <int NT>
+template <int NT, int OP>
 static size_t tcg_smem_bytes(int w_chunks) {
-  return 1024 + 2 * 2 * size_t(G_A_PART) + size_t(w_chunks) * 2 * NT * G_KC * 4 + size_t(G_STAGES) * G_RAW;
+  return 1024 + 2 * size_t(g_parts(OP)) * g_a_part(OP) + size_t(w_chunks) * g_parts(OP) * NT * G_KC * g_elt(OP) +
+         size_t(G_STAGES) * G_RAW;
+}
+
+static int tcg_op(const Plan& pl) {
+  return pl.p.precision == RAPRO_PREC_BF16 ? G_BF16 : pl.p.precision == RAPRO_PREC_FP16 ? G_FP16 : G_TF32X3;
 }
 
 constexpr size_t kTcgSmemMax = 232448;   // 227 KB, the per-CTA limit
 
-static float tf32_round_host(float x) {
-  // Round to nearest (ties away) at 10 explicit mantissa bits.
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  if ((u & 0x7f800000u) == 0x7f800000u) return x;
-  u = (u + 0x1000u) & 0xffffe000u;
-  float r;
-  std::memcpy(&r, &u, 4);
-  return r;
-}
 
 // Blocks up to 2048 subcarriers (W tiles of up to 128 MB).  The drained accumulation keeps
 // the error at that of a K = 128 sum (measured at n_sc = 1200, B = 1200: 1.6e-5 relative
@@ -403,20 +429,23 @@ constexpr int kTcgMaxBlock = 2048;
 
 bool lmmse_tcg_shape_ok(const Plan& pl) {
   const long long rows = (long long)pl.T * pl.p.K * pl.p.M;
-  return !pl.comb && pl.p.precision == RAPRO_PREC_FP32 && pl.B > 16 && pl.B <= kTcgMaxBlock && pl.B % 2 == 0 &&
-         pl.tail == 0 && rows < (1ll << 31) && pl.p.n_sc / pl.B <= 65535;
+  return !pl.comb && pl.B > 16 && pl.B <= kTcgMaxBlock && pl.B % 2 == 0 && pl.tail == 0 &&
+         rows < (1ll << 31) && pl.p.n_sc / pl.B <= 65535;
 }
 
 // Wr (2B x 2B reals) cut into tiles of NT output reals x chunks of 32 input reals, each
-// chunk TF32 hi then lo in the canonical K-major layout, tiles one after the other.
+// chunk TF32 hi then lo (or one BF16 / FP16 part) in the canonical K-major layout, tiles one
+// after the other.
 void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out) {
+  const int op = tcg_op(pl), elt = g_elt(op), np = g_parts(op);
+  const uint32_t sbo = g_sbo(op);
   const int B = pl.B, NT = tcg_nt(B), K2 = 2 * B;
   const int n_nt = (K2 + NT - 1) / NT, n_kc = (K2 + G_KC - 1) / G_KC;
-  const size_t part = size_t(NT) * G_KC * 4;
-  out.assign(size_t(n_nt) * n_kc * 2 * part, 0);
+  const size_t part = size_t(NT) * G_KC * elt;
+  out.assign(size_t(n_nt) * n_kc * np * part, 0);
   for (int t = 0; t < n_nt; ++t)
     for (int c = 0; c < n_kc; ++c) {
-      unsigned char* base = out.data() + (size_t(t) * n_kc + c) * 2 * part;
+      unsigned char* base = out.data() + (size_t(t) * n_kc + c) * np * part;
       for (int nn = 0; nn < NT; ++nn)
         for (int kk = 0; kk < G_KC; ++kk) {
           const int n = t * NT + nn, k = c * G_KC + kk;
@@ -424,10 +453,16 @@ void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out) {
           const float2 w = pl.w_main[size_t(n >> 1) * B + (k >> 1)];
           const float vals[2][2] = {{w.x, -w.y}, {w.y, w.x}};   // [out re/im][in re/im]
           const float f = vals[n & 1][k & 1];
-          const float h = tf32_round_host(f), l = tf32_round_host(f - h);
-          const size_t off = size_t((nn >> 3) * G_SBO + (kk >> 2) * 128 + (nn & 7) * 16 + (kk & 3) * 4);
-          std::memcpy(base + off, &h, 4);
-          std::memcpy(base + part + off, &l, 4);
+          const int ce = 16 / elt;                        // reals per 16-byte core row
+          const size_t off = size_t((nn >> 3) * sbo + (kk / ce) * 128 + (nn & 7) * 16 + (kk % ce) * elt);
+          if (op == G_TF32X3) {
+            const float h = tf32_round_host(f), l = tf32_round_host(f - h);
+            std::memcpy(base + off, &h, 4);
+            std::memcpy(base + part + off, &l, 4);
+          } else {
+            const uint16_t v16 = op == G_FP16 ? f16_round_host(f) : bf16_round_host(f);
+            std::memcpy(base + off, &v16, 2);
+          }
         }
     }
 }
@@ -451,7 +486,7 @@ bool lmmse_tcg_ok(const Plan& pl, const float2* x, const float2* out) {
   return pl.d_w_tcg != nullptr && (a & 15) == 0 && lmmse_tcg_shape_ok(pl) && tcg_encode() != nullptr;
 }
 
-template <int NT>
+template <int NT, int OP>
 static cudaError_t launch_tcg_nt(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st) {
   const int B = pl.B, N = pl.p.n_sc, M = pl.p.M, R = pl.T * pl.p.K * pl.p.M;
   const int n_nt = (2 * B + NT - 1) / NT, n_kc = (2 * B + G_KC - 1) / G_KC;
@@ -472,20 +507,28 @@ static cudaError_t launch_tcg_nt(const Plan& pl, const float2* x, const float2* 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int n_tiles = int(tiles), grid = std::min(n_tiles, sms);   // one CTA per SM (shared memory)
-  const int w_resident = n_nt == 1 && n_kc > 2 && tcg_smem_bytes<NT>(n_kc) <= kTcgSmemMax ? 1 : 0;
-  const size_t smem = tcg_smem_bytes<NT>(w_resident ? n_kc : 2);
+  const int w_resident = n_nt == 1 && n_kc > 2 && tcg_smem_bytes<NT, OP>(n_kc) <= kTcgSmemMax ? 1 : 0;
+  const size_t smem = tcg_smem_bytes<NT, OP>(w_resident ? n_kc : 2);
   const unsigned char* w = static_cast<const unsigned char*>(pl.d_w_tcg);
   if (pil)
-    lmmse_tcg_kernel<NT, true><<<grid, G_THREADS, smem, st>>>(map, pil, out, w, R, M, N, B, n_kc, n_rt, n_nt,
-                                                              n_tiles, w_resident, pl.d_status);
+    lmmse_tcg_kernel<NT, true, OP><<<grid, G_THREADS, smem, st>>>(map, pil, out, w, R, M, N, B, n_kc, n_rt, n_nt,
+                                                                  n_tiles, w_resident, pl.d_status);
+  else if constexpr (OP == G_TF32X3)
+    lmmse_tcg_kernel<NT, false, OP><<<grid, G_THREADS, smem, st>>>(map, pil, out, w, R, M, N, B, n_kc, n_rt,
+                                                                   n_nt, n_tiles, w_resident, pl.d_status);
   else
-    lmmse_tcg_kernel<NT, false><<<grid, G_THREADS, smem, st>>>(map, pil, out, w, R, M, N, B, n_kc, n_rt, n_nt,
-                                                               n_tiles, w_resident, pl.d_status);
+    return cudaErrorNotSupported;                    // the 16-bit forms take the LS-fused input only
   return cudaGetLastError();
 }
 
 cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st) {
-  return tcg_nt(pl.B) == 96 ? launch_tcg_nt<96>(pl, x, pil, out, st) : launch_tcg_nt<128>(pl, x, pil, out, st);
+  const bool n96 = tcg_nt(pl.B) == 96;
+  switch (tcg_op(pl)) {
+    case G_BF16: return n96 ? launch_tcg_nt<96, G_BF16>(pl, x, pil, out, st) : launch_tcg_nt<128, G_BF16>(pl, x, pil, out, st);
+    case G_FP16: return n96 ? launch_tcg_nt<96, G_FP16>(pl, x, pil, out, st) : launch_tcg_nt<128, G_FP16>(pl, x, pil, out, st);
+    default:
+      return n96 ? launch_tcg_nt<96, G_TF32X3>(pl, x, pil, out, st) : launch_tcg_nt<128, G_TF32X3>(pl, x, pil, out, st);
+  }
 }
 
 cudaError_t prepare_lmmse_tcg(int device) {
@@ -494,10 +537,15 @@ cudaError_t prepare_lmmse_tcg(int device) {
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   std::call_once(flags[device], [device] {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true>, A, int(kTcgSmemMax));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, false>, A, int(kTcgSmemMax));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true>, A, int(kTcgSmemMax));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, false>, A, int(kTcgSmemMax));
+    const int S = int(kTcgSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true, G_TF32X3>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, false, G_TF32X3>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_TF32X3>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, false, G_TF32X3>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true, G_BF16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_BF16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true, G_FP16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_FP16>, A, S);
     result[device] = e;
   });
   return result[device];

@@ -259,9 +259,9 @@ rapro_status rapro_params_validate(const rapro_params* p) {
   }
   if (p->qam_bits != 2 && p->qam_bits != 4 && p->qam_bits != 6) return invalid("qam_bits must be 2, 4 or 6");
   if (half_precision(*p)) {
-    if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL || p->subblock % 2 != 0 || p->subblock > 16 ||
+    if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL || p->subblock % 2 != 0 || p->subblock > 2048 ||
         p->n_sc % p->subblock != 0) {
-      set_error("the BF16 / FP16 forms filter on the tensor cores: orthogonal pilots, even subblock <= 16 dividing n_sc");
+      set_error("the BF16 / FP16 forms filter on the tensor cores: orthogonal pilots, even subblock <= 2048 dividing n_sc");
       return RAPRO_ERR_UNSUPPORTED;
     }
   } else if (p->precision != RAPRO_PREC_FP32) {

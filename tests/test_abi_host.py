@@ -140,12 +140,15 @@ def test_precision_validation(lib):
     p = params_for(synth.PAPER_SCALE, 12)
     p.precision = R.RAPRO_PREC_BF16
     assert R.rapro_params_validate(p) == R.RAPRO_OK
-    for B in (7, 48, 13):                  # odd, > 16, not dividing 1200
+    for B in (7, 13, 1199):                # odd, not dividing 1200
         p.subblock = B
         assert R.rapro_params_validate(p) == R.RAPRO_ERR_UNSUPPORTED
+    for B in (48, 100, 1200):              # the large-block tensor-core GEMM
+        p.subblock = B
+        assert R.rapro_params_validate(p) == R.RAPRO_OK
     p.subblock, p.precision = 12, R.RAPRO_PREC_FP16
     assert R.rapro_params_validate(p) == R.RAPRO_OK
-    for B in (7, 48, 13):
+    for B in (7, 13, 1199):
         p.subblock = B
         assert R.rapro_params_validate(p) == R.RAPRO_ERR_UNSUPPORTED
     p.subblock, p.precision = 12, 5

@@ -549,7 +549,10 @@ HALF_FORMS = {"bf16": (R.RAPRO_PREC_BF16, TOL_BF16), "fp16": (R.RAPRO_PREC_FP16,
 
 @pytest.mark.parametrize("form", list(HALF_FORMS))
 @pytest.mark.parametrize("case", [(8, 2, 72, 128, 12), (5, 3, 100, 256, 10), (6, 2, 96, 128, 16),
-                                  (2, 1, 64, 128, 2), (128, 12, 1200, 2048, 12)])
+                                  (2, 1, 64, 128, 2), (128, 12, 1200, 2048, 12),
+                                  # larger blocks: the tensor-core GEMM with 16-bit operands
+                                  (20, 3, 72, 128, 18), (7, 2, 96, 128, 48), (16, 2, 200, 256, 100),
+                                  (33, 4, 240, 512, 80), (128, 12, 1200, 2048, 1200)])
 def test_bf16_estimator_parity(case, form):
     M, K, N, nfft, B = case
     sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=24 if nfft >= 2048 else 6,
@@ -572,12 +575,14 @@ def test_bf16_estimator_parity(case, form):
         R.rapro_ce_lmmse_subblock(plan, _dev(synth.as_c64(h_ls)), h)
 
 
+@pytest.mark.parametrize("B", [12, 48, 1200])
 @pytest.mark.parametrize("form", list(HALF_FORMS))
-def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db(form):
-    """Precision forms on the paper-scale shape (64-QAM, 25 dB, several subframes): channel
-    NMSE and post-detection EVM within 0.1 dB of the FP64 oracle's."""
+def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db(form, B):
+    """Precision forms on the paper-scale shape (64-QAM, 25 dB, several subframes) at small,
+    medium and full-LMMSE blocks: channel NMSE and post-detection EVM within 0.1 dB of the
+    FP64 oracle's."""
     sh = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "snr_db": 25.0, "qam_bits": 6})
-    p = params_for(sh, 12)
+    p = params_for(sh, B)
     p.precision = HALF_FORMS[form][0]
     plan = R.Plan(p)
     s = plan.shapes()
@@ -587,7 +592,7 @@ def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db(form):
         x = torch.empty(s["x_eq"], dtype=torch.complex64, device="cuda")
         h = torch.empty(s["h"], dtype=torch.complex64, device="cuda")
         R.rapro_receive_subframe(plan, _dev(c64["y_pilot"]), _dev(c64["pilots"]), _dev(c64["y_data"]), x, h_out=h)
-        o = oracle_receive(sh, c64, 12)
+        o = oracle_receive(sh, c64, B)
         H = np.transpose(sf["H"], (1, 0, 2))[None]
         err_h += np.sum(np.abs(_host(h) - H) ** 2)
         err_h_o += np.sum(np.abs(o["h"] - H) ** 2)
