@@ -120,19 +120,20 @@ def measured_traffic(kernel):
 
 
 # ------------------------------------------------- batched heterogeneous workload
-def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3):
+def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3, bf16=False):
     """512 jobs: M ~ U{32,64,128,256}, K ~ U{4,8,12,16}, n_sc ~ U{72,300,600,1200} (FFT the next of
     128/512/1024/2048), 2/4/6-bit QAM, SNR ~ U[0,25] dB, tau ~ U[2,12], B ~ U{12,48}; inputs are
     seeded device Gaussians with unit-modulus pilots (the kernels' work does not depend on the
     values).  One CUDA graph of rapro_receive_batch over all jobs, 8 streams vs 1 stream, and
-    after rapro_plan_tune on every plan."""
+    after rapro_plan_tune on every plan.  bf16: each job's filter in the BF16 form where its
+    shape allows it (B dividing n_sc), else FP32."""
     import torch
     from paper_1802_05427_gb300 import rapro as R
     rng = np.random.default_rng(seed)
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     fft_of = {72: 128, 300: 512, 600: 1024, 1200: 2048}
-    jobs, res = [], 0
+    jobs, res, n_bf16 = [], 0, 0
     for _ in range(n_jobs):
         M = int(rng.choice([32, 64, 128, 256]))
         K = int(rng.choice([4, 8, 12, 16]))
@@ -143,6 +144,11 @@ def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3):
         B = int(rng.choice([12, 48]))
         p = R.make_params(M=M, K=K, n_sc=N, n_fft=fft_of[N], subblock=B, sigma2=10 ** (-snr / 10), qam_bits=q,
                           n_taps=16, tau_rms=tau)
+        if bf16:
+            p.precision = R.RAPRO_PREC_BF16
+            if R.rapro_params_validate(p) != R.RAPRO_OK:
+                p.precision = R.RAPRO_PREC_FP32
+            n_bf16 += p.precision == R.RAPRO_PREC_BF16
         pl = R.Plan(p)
         s = pl.shapes()
 
@@ -177,7 +183,7 @@ def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3):
         batch.close()
         return e0.elapsed_time(e1) / reps
 
-    ms8, ms1 = timed(8), timed(1)
+    ms8, ms1 = timed(8), (timed(1) if not bf16 else 0.0)
     t0 = time.time()
     for j in jobs:
         s = j["plan"].shapes()
@@ -192,6 +198,9 @@ def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3):
     for j in jobs:
         assert j["plan"].device_status() == 0
         j["plan"].close()
+    if bf16:
+        return {"jobs": n_jobs, "bf16_jobs": int(n_bf16), "ms_per_batch_8_streams": ms8,
+                "res_per_s_8_streams": res / (ms8 * 1e-3), "res_per_s_8_streams_tuned": res / (ms8t * 1e-3)}
     return {"jobs": n_jobs, "res_per_batch": res, "ms_per_batch_8_streams": ms8, "ms_per_batch_1_stream": ms1,
             "res_per_s_8_streams": res / (ms8 * 1e-3), "res_per_s_1_stream": res / (ms1 * 1e-3),
             "res_per_s_8_streams_tuned": res / (ms8t * 1e-3), "tune_seconds": tune_s,
@@ -689,6 +698,7 @@ def run_rapro(args):
     hetero = {}
     if want("hetero") and rank == 0 and world == 1:
         hetero = hetero_batch(dev)
+        hetero["bf16_filter_where_allowed"] = hetero_batch(dev, bf16=True)
 
     # 64 paper-scale subframes in one rapro_receive_batch call (one plan, 8 library streams,
     # one CUDA graph per batch; the inputs rotate over the resident sets, every job has its
