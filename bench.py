@@ -95,6 +95,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def tf32x3_peak():
+    """Peak rate of FP32-accurate algorithmic flops on the tensor cores: the TF32 dense rate
+    (measured BF16 burst x the nominal TF32 / BF16 ratio 1.1 / 2.25) over the 3 TF32 passes."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16, kind = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        bf16, kind = 1900.0, "fallback"
+    return bf16 * 1.1 / 2.25 / 3.0, f"{kind} BF16 {bf16:g} TFLOP/s x 1.1/2.25 (TF32) / 3 passes"
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1802_05427_gb300", "csrc")
@@ -789,22 +800,31 @@ def run_rapro(args):
     value = whole_job_value(world, res_per_step, args.steps, ms)
     hbm, peak_kind = peaks()
     rows = {}
+    # the estimator runs on the tensor cores (3 TF32 passes) for every even B <= 2048 dividing
+    # n_sc; its compute roof is then the tensor rate, not the FP32 FMA rate
+    est_on_tc = B % 2 == 0 and sh.n_sc % B == 0 and B <= 2048
+    tc_peak, tc_src = tf32x3_peak()
     for name, us in (("ls_lmmse", us_est), ("detect", us_det)):
         a = alg[name]
         t_hbm = a["bytes"] / (hbm * 1e9)
-        t_alu = a["flops"] / (ALU_PEAK_TFLOPS * 1e12)
+        on_tc = name == "ls_lmmse" and est_on_tc
+        cpeak = tc_peak if on_tc else ALU_PEAK_TFLOPS
+        t_alu = a["flops"] / (cpeak * 1e12)
         if t_hbm >= t_alu:
             ach, peak, unit, bound = a["bytes"] / (us * 1e-6) / 1e9, hbm, "GB/s", "hbm"
         else:
-            ach, peak, unit, bound = a["flops"] / (us * 1e-6) / 1e12, ALU_PEAK_TFLOPS, "TFLOP/s", "alu"
+            ach, peak, unit, bound = a["flops"] / (us * 1e-6) / 1e12, cpeak, "TFLOP/s", "tensor" if on_tc else "alu"
         rows[name] = dict(bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
                           us_per_launch=us, alg_bytes=a["bytes"], alg_flops=a["flops"])
+        if on_tc:
+            rows[name]["tensor_peak_source"] = tc_src
     dom = max(rows, key=lambda k: rows[k]["us_per_launch"])
     r = rows[dom]
     traffic = measured_traffic(dom)
     roof = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
             "frac": r["frac"], "traffic": traffic, "kernel": dom,
             "peak_source": (f"{peak_kind} HBM copy bandwidth" if r["bound"] == "hbm" else
+                            tc_src if r["bound"] == "tensor" else
                             "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)")}
     # the path against its own roofline: t_roof = max(bytes / HBM, flops / FP32 FMA peak)
     pa = alg["path"]
