@@ -106,6 +106,24 @@ def tf32x3_peak():
     return bf16 * 1.1 / 2.25 / 3.0, f"{kind} BF16 {bf16:g} TFLOP/s x 1.1/2.25 (TF32) / 3 passes"
 
 
+def roof_row(a, us, hbm, on_tc):
+    """One kernel against its roofline: the larger of its algorithmic bytes over the HBM
+    copy rate and its flops over the rate of the unit that does them (FP32 FMA, or the
+    FP32-accurate tensor rate when on_tc); achieved = the same quantity over the measured
+    launch time us (microseconds)."""
+    tc_peak, tc_src = tf32x3_peak()
+    cpeak = tc_peak if on_tc else ALU_PEAK_TFLOPS
+    if a["bytes"] / (hbm * 1e9) >= a["flops"] / (cpeak * 1e12):
+        ach, peak, unit, bound = a["bytes"] / (us * 1e-6) / 1e9, hbm, "GB/s", "hbm"
+    else:
+        ach, peak, unit, bound = a["flops"] / (us * 1e-6) / 1e12, cpeak, "TFLOP/s", "tensor" if on_tc else "alu"
+    row = dict(bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak, us_per_launch=us,
+               alg_bytes=a["bytes"], alg_flops=a["flops"])
+    if on_tc:
+        row["tensor_peak_source"] = tc_src
+    return row
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1802_05427_gb300", "csrc")
@@ -803,21 +821,9 @@ def run_rapro(args):
     # the estimator runs on the tensor cores (3 TF32 passes) for every even B <= 2048 dividing
     # n_sc; its compute roof is then the tensor rate, not the FP32 FMA rate
     est_on_tc = B % 2 == 0 and sh.n_sc % B == 0 and B <= 2048
-    tc_peak, tc_src = tf32x3_peak()
+    tc_src = tf32x3_peak()[1]
     for name, us in (("ls_lmmse", us_est), ("detect", us_det)):
-        a = alg[name]
-        t_hbm = a["bytes"] / (hbm * 1e9)
-        on_tc = name == "ls_lmmse" and est_on_tc
-        cpeak = tc_peak if on_tc else ALU_PEAK_TFLOPS
-        t_alu = a["flops"] / (cpeak * 1e12)
-        if t_hbm >= t_alu:
-            ach, peak, unit, bound = a["bytes"] / (us * 1e-6) / 1e9, hbm, "GB/s", "hbm"
-        else:
-            ach, peak, unit, bound = a["flops"] / (us * 1e-6) / 1e12, cpeak, "TFLOP/s", "tensor" if on_tc else "alu"
-        rows[name] = dict(bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
-                          us_per_launch=us, alg_bytes=a["bytes"], alg_flops=a["flops"])
-        if on_tc:
-            rows[name]["tensor_peak_source"] = tc_src
+        rows[name] = roof_row(alg[name], us, hbm, name == "ls_lmmse" and est_on_tc)
     dom = max(rows, key=lambda k: rows[k]["us_per_launch"])
     r = rows[dom]
     traffic = measured_traffic(dom)

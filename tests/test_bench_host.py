@@ -57,3 +57,24 @@ def test_algorithmic_bytes_and_flops_of_the_paper_scale_subframe():
     det = a["detect"]
     assert det["bytes"] == 8 * n_h + 8 * 12 * 128 * 1200 + 8 * 12 * 12 * 1200 + 12 * 12 * 1200 + 4 * 2 * 1200
     assert det["flops"] == 2400 * (8 * 128 * 78 + 8 * 12 ** 3 // 6) + 14400 * (8 * 128 * 12 + 8 * 144)
+
+
+def test_roofline_rows_pick_the_binding_unit():
+    """The estimator on tcgen05 is bound by HBM at B = 12 and by the FP32-accurate tensor rate
+    at B = 1200 (flops / us / peak); the detector compares against HBM and FP32 FMA."""
+    from paper_1802_05427_gb300 import synth
+    sh = synth.PAPER_SCALE
+    hbm = 6693.5
+    tc_peak = bench.tf32x3_peak()[0]
+    assert 300.0 < tc_peak < 340.0          # 1960.2 x 1.1 / 2.25 / 3 with the committed peaks
+    a12 = bench.algorithmic(sh, 12)["ls_lmmse"]
+    r = bench.roof_row(a12, 19.2, hbm, True)
+    assert r["bound"] == "hbm" and abs(r["frac"] - a12["bytes"] / 19.2e-6 / 1e9 / hbm) < 1e-12
+    a1200 = bench.algorithmic(sh, 1200)["ls_lmmse"]
+    r = bench.roof_row(a1200, 258.7, hbm, True)
+    assert r["bound"] == "tensor" and r["peak"] == tc_peak
+    assert abs(r["frac"] - a1200["flops"] / 258.7e-6 / 1e12 / tc_peak) < 1e-12
+    r = bench.roof_row(a1200, 258.7, hbm, False)  # the same work on the FP32 cores
+    assert r["bound"] == "alu" and r["peak"] == bench.ALU_PEAK_TFLOPS
+    d = bench.algorithmic(sh, 12)["detect"]
+    assert bench.roof_row(d, 24.4, hbm, False)["bound"] == "hbm"
