@@ -1,5 +1,6 @@
 // LS + sub-block LMMSE (Eq. 9, 12, 17) for large blocks as a GEMM on the 5th-generation
-// tensor cores (tcgen05), FP32 accuracy from three TF32 passes.
+// tensor cores (tcgen05): FP32 accuracy from three TF32 passes, or the precision forms'
+// single pass of BF16 / FP16 operands.
 //
 // With B dividing n_sc all blocks share W, and block b of every row r = (slot, user,
 // antenna) is one row of the product
@@ -10,13 +11,15 @@
 // runs of tiles:
 //  * a copy warp brings each raw chunk (128 rows x 16 complex of y_pilot, or of h_ls) by a
 //    2-D TMA box into a 4-stage ring, and the matching chunk of Wr (NT x 32 reals, TF32 hi
-//    then lo, laid out on the host in the canonical K-major layout) by one bulk copy into
-//    one of two W buffers;
+//    then lo or one 16-bit part, laid out on the host in the canonical K-major layout) by
+//    one bulk copy into one of two W buffers (a single column tile's W stays resident);
 //  * 256 consumer threads apply LS (y conj(p) / |p|^2) and split each value into TF32
-//    hi + lo (both rounded to nearest) in the canonical layout of one of two A buffers;
-//  * one MMA thread issues 4 K-steps x 3 passes (Ah Wh + Ah Wl + Al Wh, M = 128, N = NT,
-//    K = 8) per chunk into one of two FP32 accumulators in tensor memory and commits each
-//    chunk to an mbarrier, which frees that chunk's A and W buffers;
+//    hi + lo (both rounded to nearest), or round it to BF16 / FP16, in the canonical layout
+//    of one of two A buffers;
+//  * one MMA thread issues the chunk's K-steps (TF32: 4 x 3 passes Ah Wh + Ah Wl + Al Wh,
+//    K = 8; 16-bit: 2 x 1 pass, K = 16; M = 128, N = NT) into one of two FP32 accumulators in
+//    tensor memory and commits each chunk to an mbarrier, which frees that chunk's A and W
+//    buffers;
 // and every G_DR chunks the consumers drain the accumulator (TMEM lane = row) into FP32
 // registers while the next group's MMAs run in the other one, storing their row's outputs
 // after a tile's last group.  Only mbarriers order the roles; every wait is bounded.
@@ -88,9 +91,9 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// x rounded to nearest at TF32 (ties away from zero).  Over K = 2B up to thousands of terms a
-// truncating split would leave errors of one sign that add up linearly; rounded hi and lo
-// parts leave unbiased residuals of at most 2^-22 |x|.
+// x rounded to nearest at TF32 (ties away from zero): rounded hi and lo parts leave unbiased
+// residuals of at most 2^-22 |x| (a truncating split biases them; the tensor cores' own
+// accumulation error over a long K is bounded by draining, G_DR).
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -103,11 +106,12 @@ __host__ __device__ constexpr int tmem_cols(int nt) { return nt <= 32 ? 32 : nt 
 
 // NT: output reals per tile (a multiple of 32, at most 128).  LS: the input is y_pilot and
 // LS is applied on load (else the input is h_ls).  OP: operand form (G_TF32X3, G_BF16,
-// G_FP16; the 16-bit forms are one pass with no lo parts).  Persistent: CTA i takes the contiguous
-// run of output tiles [n_tiles i / grid, n_tiles (i + 1) / grid), tile index = (block, row
-// tile, column tile) with the column tile fastest (the row tile's chunks stay in L2 for the
+// G_FP16; the 16-bit forms are one pass with no lo parts).  Persistent: CTA i takes the
+// contiguous run of output tiles [n_tiles i / grid, n_tiles (i + 1) / grid), tile index =
+// (block, row tile, column tile) with the column tile fastest (the row tile's chunks stay in L2 for the
 // next column tile); the chunks of all its tiles form one stream through the ring, and two
-// accumulators in tensor memory let one tile's read-back overlap the next tile's MMAs.
+// accumulators in tensor memory let one drain group's read-back overlap the next group's
+// MMAs.
 template <int NT, bool LS, int OP>
 __global__ void __launch_bounds__(G_THREADS, 1)
     lmmse_tcg_kernel(const __grid_constant__ CUtensorMap map_x, const float2* __restrict__ pil,
