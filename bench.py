@@ -369,11 +369,15 @@ def cpu_baseline(sh, B, target_s=12.0):
         per_sub = max(dt, 1e-3)
         n_sub = max(1, int(target_s / per_sub))
         out = pool.map(_oracle_job, [(shape_kw, B, sh.n_sc, n_sub, 7100 + i) for i in range(n)])
+        # one process alone: the single-core rate
+        res1, dt1 = pool.map(_oracle_job, [(shape_kw, B, sh.n_sc, 1, 7200)])[0]
     res_total = sum(r for r, _ in out)
     t = max(d for _, d in out)
     return {"value": res_total / t, "unit": UNIT, "cores": n, "kind": "oracle",
             "sample": f"{n} processes x {n_sub} full subframes each (1 BLAS thread per process), "
-                      f"{res_total} REs in {t:.1f} s"}
+                      f"{res_total} REs in {t:.1f} s",
+            "single_core": {"value": res1 / max(dt1, 1e-9), "unit": UNIT,
+                            "sample": f"1 process, 1 BLAS thread, 1 full subframe ({res1} REs in {dt1:.2f} s)"}}
 
 
 # ----------------------------------------------------------- reference arm
