@@ -1,5 +1,6 @@
 """CPU tests of the C-ABI library: it builds, loads, exports what rapro.h declares, and its
 host-side logic (parameter checks, FP64 weights) behaves.  No GPU calls."""
+import ctypes
 import os
 import subprocess
 
@@ -177,3 +178,31 @@ def test_host_weight_gradient_matches_autograd(lib, B):
                                          G.block_weight(tail, s2, tau, sh.n_taps, sh.n_fft)))
     f.backward()
     np.testing.assert_allclose([d_s2, d_tau], [float(s2.grad), float(tau.grad)], rtol=1e-9, atol=1e-12)
+
+
+NULL_HANDLE_CALLS = [
+    ("rapro_plan_dims", 5), ("rapro_plan_device_status", 3), ("rapro_ce_ls", 5),
+    ("rapro_ce_lmmse_subblock", 5), ("rapro_ce_ls_lmmse", 6), ("rapro_mmse_detect", 8),
+    ("rapro_ce_comb", 5), ("rapro_receive_subframe", 10), ("rapro_mse_backward", 12),
+    ("rapro_plan_tune", 7), ("rapro_plan_variant", 4), ("rapro_plan_set_variant", 4),
+    ("rapro_plan_set_receive_form", 2), ("rapro_receive_is_fused", 4), ("rapro_receive_batch", 4),
+    ("rapro_receive_subframe_noalloc", 9), ("rapro_plan_create", 2), ("rapro_batch_create", 2),
+]
+
+
+@pytest.mark.parametrize("name,n_args", NULL_HANDLE_CALLS, ids=[c[0] for c in NULL_HANDLE_CALLS])
+def test_null_handles_are_rejected_before_any_device_work(lib, name, n_args):
+    """A NULL plan, batch, params or output handle returns RAPRO_ERR_INVALID_ARG with a message;
+    the check precedes every CUDA call, so it runs here without a GPU."""
+    f = getattr(lib, name)
+    assert len(f.argtypes) == n_args
+    args = [0 if t is ctypes.c_int else None for t in f.argtypes]
+    if name == "rapro_batch_create":
+        args[0] = 1                                  # a valid stream count, NULL out
+    assert f(*args) == R.RAPRO_ERR_INVALID_ARG
+    assert lib.rapro_last_error().decode()
+
+
+def test_null_destroy_is_a_no_op(lib):
+    assert lib.rapro_plan_destroy(None) == R.RAPRO_OK
+    assert lib.rapro_batch_destroy(None) == R.RAPRO_OK
