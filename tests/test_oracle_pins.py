@@ -364,6 +364,59 @@ def test_llr_closed_forms_and_signs():
             assert np.all((ll[nz, i] > 0) == (bit[nz] == 0))
 
 
+def _pam_maxlog_closed_form(y, s0):
+    """Max-log LLR of one Gray PAM bit on the integer grid (levels odd integers), written as
+    the exact piecewise-linear forms of the Gray 4- and 8-PAM demappers; s0 = the levels
+    where the bit is 0.  Returns None for a level set that is not one of those forms."""
+    a = np.abs(y)
+    sg = np.sign(y)
+    s0 = frozenset(s0)
+    forms = {
+        # 4-PAM (16-QAM per dimension)
+        frozenset({1, 3}): np.where(a <= 2, 4 * y, 8 * (y - sg)),
+        frozenset({-1, 1}): 4 * (2 - a),
+        # 8-PAM (64-QAM per dimension)
+        frozenset({1, 3, 5, 7}): np.select([a <= 2, a <= 4, a <= 6],
+                                           [4 * y, 8 * (y - sg), 12 * (y - 2 * sg)], 16 * (y - 3 * sg)),
+        frozenset({-3, -1, 1, 3}): np.select([a <= 2, a <= 6], [8 * (3 - a), 4 * (4 - a)], 8 * (5 - a)),
+        frozenset({-7, -1, 1, 7}): 4 * (np.abs(a - 4) - 2),
+    }
+    if s0 in forms:
+        return forms[s0]
+    levels = frozenset(range(-7, 8, 2)) if max(s0) > 3 or min(s0) < -3 else frozenset({-3, -1, 1, 3})
+    comp = levels - s0
+    if comp in forms:
+        return -forms[comp]
+    return None
+
+
+@pytest.mark.parametrize("q", [4, 6])
+def test_llr_matches_gray_pam_piecewise_linear_forms(q):
+    """Every bit of the 16- and 64-QAM max-log LLR against the exact per-dimension piecewise
+    linear forms of Gray PAM (Eq. 22 read as max-log over the product constellation)."""
+    m = q // 2
+    scale = np.sqrt(2.0 * (4 ** m - 1) / 3.0)          # unit mean energy: levels / scale
+    rng = np.random.default_rng(11 + q)
+    y = rng.uniform(-(1 << m) - 2, (1 << m) + 2, (2, 3000))
+    xhat = (y[0] + 1j * y[1]) / scale
+    nu = rng.uniform(0.05, 2.0, 3000)
+    llr = O.maxlog_llr(xhat, nu, q)
+    pts = O.constellation(q)
+    labels = np.arange(1 << q)
+    for i in range(q):
+        bit = (labels >> (q - 1 - i)) & 1
+        for dim, part in enumerate((np.real, np.imag)):
+            lv = np.rint(part(pts) * scale).astype(int)
+            if all(len(set(bit[lv == v])) == 1 for v in set(lv)):   # this bit lives on `dim`
+                s0 = {int(v) for v in set(lv[bit == 0])}
+                f = _pam_maxlog_closed_form(y[dim], s0)
+                assert f is not None, (q, i, s0)
+                np.testing.assert_allclose(llr[:, i], f / (scale ** 2 * nu), rtol=1e-11, atol=1e-11)
+                break
+        else:
+            raise AssertionError(f"bit {i} of {q}-bit labels depends on both dimensions")
+
+
 def test_boundary_margin_units():
     for q in (2, 4, 6):
         pts = O.constellation(q)
