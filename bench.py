@@ -410,8 +410,10 @@ def run_reference(args):
             "config": {"workload": desc, "subblock": B, "snr_db": sh.snr_db},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle",
-                             "sample": f"each step: {n} processes x 1 subframe restricted to the first {n_sc} "
-                                       f"subcarriers ({n_sc // B} blocks of {B}); inputs drawn once "
+                             "sample": f"each step: {n} processes x 1 "
+                                       + ("full subframe" if n_sc == sh.n_sc else
+                                          f"subframe restricted to the first {n_sc} subcarriers")
+                                       + f" ({n_sc // B} blocks of {B}); inputs drawn once "
                                        "per worker outside the timing"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
