@@ -206,3 +206,29 @@ def test_null_handles_are_rejected_before_any_device_work(lib, name, n_args):
 def test_null_destroy_is_a_no_op(lib):
     assert lib.rapro_plan_destroy(None) == R.RAPRO_OK
     assert lib.rapro_batch_destroy(None) == R.RAPRO_OK
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No CPU fallback: a missing librapro.so is an ImportError, not a silent path."""
+    monkeypatch.setattr(R, "_lib", None)
+    monkeypatch.setattr(R, "LIB_PATH", os.path.join(os.path.dirname(R.LIB_PATH), "no_such_librapro.so"))
+    with pytest.raises(ImportError, match="missing"):
+        R.lib()
+
+
+def test_binding_rejects_host_tensors(lib):
+    """Arrays must be CUDA tensors of the declared dtype, shape and layout; a host tensor is a
+    TypeError raised before any library call (the kernels are the only compute path)."""
+    import torch
+    p = _good()
+    T, D = p.n_pilot_sym, p.n_sym // p.n_pilot_sym - 1
+    K, M, N = p.K, p.M, p.n_sc
+    c64 = torch.complex64
+    host = dict(y_pilot=torch.zeros(T, K, M, N, dtype=c64), pilots=torch.ones(T, K, N, dtype=c64),
+                y_data=torch.zeros(T * D, M, N, dtype=c64), x_eq=torch.zeros(T * D, K, N, dtype=c64))
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        R.rapro_receive_subframe_noalloc(p, **host)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        R._ptr(host["x_eq"], (T * D, K, N), c64, "x_eq")
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        R._ptr(np.zeros((T * D, K, N), np.complex64), (T * D, K, N), c64, "x_eq")
