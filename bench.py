@@ -37,8 +37,11 @@ UNIT = "REs/s"
 N_SETS = 8                   # resident input subframes rotated through (> L2 in total)
 GRAPH_STEPS = 3 * N_SETS     # steps per captured CUDA graph
 IN_FLIGHT = 4                # subframes in flight: consecutive steps rotate over 4 streams
+MAX_GRAPH_STEPS = 1024       # steps per graph of the timed region
 L2_BYTES = 129 * 2 ** 20
-ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+# FP32 FMA lanes x 2 flop x max SM clock: context, and the fallback when the measured rate
+# (rapro_measure_ffma_peak, taken by every run) is not available
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def parse():
@@ -106,13 +109,13 @@ def tf32x3_peak():
     return bf16 * 1.1 / 2.25 / 3.0, f"{kind} BF16 {bf16:g} TFLOP/s x 1.1/2.25 (TF32) / 3 passes"
 
 
-def roof_row(a, us, hbm, on_tc):
+def roof_row(a, us, hbm, on_tc, alu_peak=None):
     """One kernel against its roofline: the larger of its algorithmic bytes over the HBM
-    copy rate and its flops over the rate of the unit that does them (FP32 FMA, or the
-    FP32-accurate tensor rate when on_tc); achieved = the same quantity over the measured
-    launch time us (microseconds)."""
+    copy rate and its flops over the rate of the unit that does them (FP32 FMA at alu_peak
+    TFLOP/s, measured, else the derived figure; or the FP32-accurate tensor rate when on_tc);
+    achieved = the same quantity over the measured launch time us (microseconds)."""
     tc_peak, tc_src = tf32x3_peak()
-    cpeak = tc_peak if on_tc else ALU_PEAK_TFLOPS
+    cpeak = tc_peak if on_tc else (alu_peak or ALU_PEAK_TFLOPS)
     if a["bytes"] / (hbm * 1e9) >= a["flops"] / (cpeak * 1e12):
         ach, peak, unit, bound = a["bytes"] / (us * 1e-6) / 1e9, hbm, "GB/s", "hbm"
     else:
@@ -237,6 +240,33 @@ def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3, bf16=False):
             "inputs": "seeded device Gaussians (unit-modulus pilots), one CUDA graph per batch"}
 
 
+def measure_ffma(R, dev, trips=50000, runs=5):
+    """FP32 FMA peak of this GPU: the library's FMA-chain probe (full occupancy, 8
+    independent chains per thread), best of `runs` launches, with the SM clock sampled
+    during them; flop_per_clk_per_sm checks the figure against 2 x 128 lanes."""
+    import torch
+    clocks = ClockSampler(gpu_id_for(dev))
+    clocks.start()
+    time.sleep(0.3)
+    R.rapro_measure_ffma_peak(2000)
+    t0 = time.time()
+    got = [R.rapro_measure_ffma_peak(trips) for _ in range(runs)]
+    t1 = time.time()
+    time.sleep(0.2)
+    clocks.stop()
+    clk = clocks.summary(t0, t1, "the probe's launches")
+    tf = max(g[0] for g in got)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {"tflops": tf, "tflops_median": statistics.median(g[0] for g in got),
+           "ms_per_launch": statistics.median(g[1] for g in got), "sms": sms, "clocks": clk,
+           "derived_at_max_clock_tflops": sms * 128 * 2 * 2.070e9 / 1e12,
+           "source": "rapro_measure_ffma_peak: 8 CTAs x 256 threads per SM, 8 independent FMA chains per "
+                     f"thread, {16 * trips} rounds, best of {runs} (CUDA events)"}
+    if clk.get("sm_mhz"):
+        out["flop_per_clk_per_sm"] = tf * 1e12 / (sms * clk["sm_mhz"] * 1e6)
+    return out
+
+
 # ------------------------------------------------------------ multi-rank
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """The largest of every rank's value (a timed region ends when the slowest rank does)."""
@@ -246,6 +276,12 @@ def max_over_ranks(value: float, dist=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def timed_pieces(steps: int) -> list:
+    """Step counts of the graphs that make up a timed region of `steps` steps."""
+    full, rest = divmod(max(int(steps), 0), MAX_GRAPH_STEPS)
+    return [MAX_GRAPH_STEPS] * full + ([rest] if rest else [])
 
 
 def whole_job_value(world: int, units_per_step: int, steps: int, ms: float) -> float:
@@ -504,16 +540,21 @@ def run_rapro(args):
         torch.cuda.synchronize()
         return g
 
-    g_full = capture(("est", "det"), GRAPH_STEPS, pipelines=IN_FLIGHT)
-    g_one = [capture(("est", "det"), 1, j) for j in range(GRAPH_STEPS)]
+    # The timed region replays graphs holding exactly --steps steps (in pieces of at most
+    # MAX_GRAPH_STEPS), each rotating consecutive steps over IN_FLIGHT streams: the region is
+    # the pipelined path at any step count, with one pipeline fill and drain per piece.
+    g_full = capture(("est", "det"), GRAPH_STEPS, pipelines=IN_FLIGHT)       # warm-up and soak
+    pieces = timed_pieces(args.steps)
+    g_timed = {n: capture(("est", "det"), n, pipelines=IN_FLIGHT) for n in sorted(set(pieces))}
+    for g in g_timed.values():            # first replays (graph upload) stay out of the region
+        g.replay()
+    torch.cuda.synchronize()
     g_est = capture(("est",), GRAPH_STEPS)
     g_det = capture(("det",), GRAPH_STEPS)
 
     def run_steps(k):
-        for _ in range(k // GRAPH_STEPS):
-            g_full.replay()
-        for j in range(k % GRAPH_STEPS):
-            g_one[j].replay()
+        for n in timed_pieces(k):
+            g_timed[n].replay()
 
     clocks = ClockSampler(gpu_id_for(dev))
     clocks.start()
@@ -521,7 +562,8 @@ def run_rapro(args):
     # sustained load before the timed region so the clock samples see a loaded GPU
     t_soak = time.time()
     while time.time() - t_soak < 1.5:
-        run_steps(GRAPH_STEPS * 16)
+        for _ in range(16):
+            g_full.replay()
         torch.cuda.synchronize()
 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -557,6 +599,7 @@ def run_rapro(args):
     reps = max(16, min(500, args.steps // GRAPH_STEPS))
     us_est, us_det = time_graph(g_est, reps), time_graph(g_det, reps)
     assert plan.device_status() == 0, "device status reports a timeout"
+    ffma = measure_ffma(R, dev)
 
     # end to end through the user API with pinned host buffers (copies inside the region)
     rx = R.Receiver(params, device=local)
@@ -828,8 +871,9 @@ def run_rapro(args):
     # n_sc; its compute roof is then the tensor rate, not the FP32 FMA rate
     est_on_tc = B % 2 == 0 and sh.n_sc % B == 0 and B <= 2048
     tc_src = tf32x3_peak()[1]
+    alu_peak = ffma["tflops"]
     for name, us in (("ls_lmmse", us_est), ("detect", us_det)):
-        rows[name] = roof_row(alg[name], us, hbm, name == "ls_lmmse" and est_on_tc)
+        rows[name] = roof_row(alg[name], us, hbm, name == "ls_lmmse" and est_on_tc, alu_peak)
     dom = max(rows, key=lambda k: rows[k]["us_per_launch"])
     r = rows[dom]
     traffic = measured_traffic(dom)
@@ -837,16 +881,29 @@ def run_rapro(args):
             "frac": r["frac"], "traffic": traffic, "kernel": dom,
             "peak_source": (f"{peak_kind} HBM copy bandwidth" if r["bound"] == "hbm" else
                             tc_src if r["bound"] == "tensor" else
-                            "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)")}
-    # the path against its own roofline: t_roof = max(bytes / HBM, flops / FP32 FMA peak)
+                            "measured FP32 FMA peak (rapro_measure_ffma_peak)")}
+    # The path against its roofline.  Binding form: the estimator's flops run on the tensor
+    # cores (3 TF32 passes) when est_on_tc, the detector's on FP32 FMA; the units work side
+    # by side, so t_roof = max(bytes / HBM, estimator flops / its unit, detector flops / FMA).
+    # The all-FMA form (every flop on FP32 FMA) is given beside it.
     pa = alg["path"]
     t_step = ms / args.steps * 1e-3
-    t_roof = max(pa["bytes"] / (hbm * 1e9), pa["flops"] / (ALU_PEAK_TFLOPS * 1e12))
-    path_roof = {"bound": "hbm" if pa["bytes"] / (hbm * 1e9) >= pa["flops"] / (ALU_PEAK_TFLOPS * 1e12) else "alu",
-                 "alg_bytes": pa["bytes"], "alg_flops": pa["flops"], "t_roof_us": t_roof * 1e6,
+    tc_peak = tf32x3_peak()[0]
+    t_bytes = pa["bytes"] / (hbm * 1e9)
+    t_est = alg["ls_lmmse"]["flops"] / ((tc_peak if est_on_tc else alu_peak) * 1e12)
+    t_det = alg["detect"]["flops"] / (alu_peak * 1e12)
+    terms = {"hbm": t_bytes, "tensor" if est_on_tc else "alu_estimator": t_est, "alu_detector": t_det}
+    bind = max(terms, key=terms.get)
+    t_roof = terms[bind]
+    t_fma = max(t_bytes, pa["flops"] / (alu_peak * 1e12))
+    path_roof = {"bound": bind, "alg_bytes": pa["bytes"], "alg_flops": pa["flops"], "t_roof_us": t_roof * 1e6,
                  "t_step_us": t_step * 1e6, "frac": t_roof / t_step,
-                 "note": "whole step (estimator + detector, subframes in flight) against max(algorithmic "
-                         "bytes / HBM peak, algorithmic flops / FP32 FMA peak)"}
+                 "terms_us": {k: v * 1e6 for k, v in terms.items()},
+                 "all_fma_form": {"t_roof_us": t_fma * 1e6, "frac": t_fma / t_step,
+                                  "bound": "hbm" if t_bytes >= t_fma else "alu"},
+                 "note": "whole step (estimator + detector, subframes in flight) against max(algorithmic bytes / "
+                         "HBM peak, estimator flops / the unit it runs on, detector flops / measured FP32 FMA "
+                         "peak); all_fma_form puts every flop on FP32 FMA"}
     ev, dsplit, egrid = R.rapro_plan_variant(plan)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -856,8 +913,9 @@ def run_rapro(args):
                        "res_per_step": res_per_step, "parallelism": f"replicas x{world}",
                        "l2": f"{N_SETS} resident input subframes rotated ({N_SETS * in_bytes / 2**20:.0f} MiB > "
                              f"{L2_BYTES / 2**20:.0f} MiB L2)",
-                       "launch": f"CUDA graph replays of {GRAPH_STEPS} steps; consecutive steps rotate "
-                                 f"over {IN_FLIGHT} streams, so {IN_FLIGHT} subframes are in flight",
+                       "launch": f"graphs of exactly {args.steps} steps (pieces of <= {MAX_GRAPH_STEPS}); "
+                                 f"consecutive steps rotate over {IN_FLIGHT} streams, so {IN_FLIGHT} "
+                                 "subframes are in flight at any step count",
                        "plan_variant": {"est_variant": ev, "det_split": dsplit, "est_ctas_per_sm": egrid}},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": whole_job_value(world, res_per_step, args.e2e_steps, e2e_ms), "unit": UNIT,
@@ -865,7 +923,7 @@ def run_rapro(args):
                     "api": "Receiver.receive_host (pinned host in/out, rapro_receive_subframe; 2 buffer sets "
                            "so one subframe's copies overlap the previous one's kernels)",
                     "host_link_gbs": h2d * args.e2e_steps / (e2e_ms * 1e-3) / 1e9},
-            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "gpu_launches": 2 * args.steps, "clocks": clk, "ffma_peak": ffma,
             "path_roofline": path_roof,
             "kernels": rows, "kernel_timing": f"graphs of {GRAPH_STEPS} launches of one kernel alone on one "
                                               "stream, same plan variant as the timed step",

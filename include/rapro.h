@@ -382,27 +382,44 @@ rapro_status rapro_weight_grad_host(const rapro_params* p, const double* g_w_mai
                                     double* grad_out);
 
 /*
+ * Measurement utility (not a step of the receive path): the device's FP32 FMA rate.
+ * Launches a full-occupancy grid (8 CTAs of 256 threads per SM) in which every thread
+ * runs 8 independent FMA recurrences for 16 x trips rounds, on `stream`, timed with CUDA
+ * events after one short warm-up launch; waits for it to finish.  *tflops_out receives
+ * 2 x FMAs / seconds / 1e12 and *ms_out (nullable) the timed launch's duration.  The SM
+ * clock during the launch decides the figure: sample it alongside.  RAPRO_ERR_INVALID_ARG
+ * if trips < 1 or tflops_out is NULL.
+ */
+rapro_status rapro_measure_ffma_peak(int trips, double* tflops_out, double* ms_out, rapro_stream stream);
+
+/*
  * Allocation-free variant of rapro_receive_subframe (the paper has no counterpart; it
  * runs its receiver on host memory it allocates freely).  For callers that cannot
- * allocate device memory when a subframe arrives: code running inside a CUDA graph
- * capture (where cudaMalloc is not allowed), real-time slot loops that must not wait on an
- * allocator, and processes whose device memory belongs to another framework's pool.
+ * allocate device memory when a subframe arrives: real-time slot loops that must not
+ * wait on an allocator (cudaMalloc can synchronise the device or take milliseconds,
+ * longer than a slot's deadline), processes whose device memory belongs to another
+ * framework's pool, and deployments that forbid run-time allocation.
  *  - Needs no plan: p is validated and the weights of its sub-block size are built in
- *    FP64 on the host at every call and passed to the kernel as parameters, so subblock
- *    must be <= 32 (RAPRO_ERR_UNSUPPORTED otherwise); the comb layout is not available
- *    here (RAPRO_ERR_UNSUPPORTED).
+ *    FP64 on the host at every call (the plan's builder, in stack storage) and passed to
+ *    the kernel as parameters, so subblock must be <= 32 (RAPRO_ERR_UNSUPPORTED
+ *    otherwise).  The comb layout and the 16-bit precision forms are not available here
+ *    (RAPRO_ERR_UNSUPPORTED): precision must be RAPRO_PREC_FP32.
  *  - The channel-estimate scratch is a fixed 32 MiB device array inside the library
  *    (held by every GPU that loads the library until the process exits):
  *    n_pilot_sym * K * M * n_sc * 8 bytes must not exceed 32 MiB (RAPRO_ERR_INVALID_ARG
  *    otherwise; the 128 x 12 x 1200 two-slot subframe needs 29.5 MB).
  *  - Allocates and frees no device memory; the only host allocation is the text of an
  *    error message on a rejected call.
- *  - The first call on a device looks up the scratch's device address and raises the
- *    detector's shared-memory limit; make that first call before any stream capture.
- *  - All calls share the scratch (it keeps the last call's contents): calls that overlap
- *    on the GPU race and give undefined outputs; serialise them.
- *  - A pipeline timeout leaves a subcarrier's outputs and info entry unwritten: a caller
- *    that must detect it fills info with a sentinel (e.g. -1) before the call.
+ *  - The first call on a device (of this function or rapro_noalloc_status) looks up the
+ *    scratch's device address and raises the kernels' shared-memory limits; make that
+ *    first call before any stream capture.
+ *  - All calls share the scratch and its status word (they keep the last call's
+ *    contents; each call clears the status word first): calls that overlap on the GPU
+ *    race and give undefined outputs; serialise them.
+ *  - A pipeline timeout is recorded in the scratch's status word (read it with
+ *    rapro_noalloc_status).  After an estimator timeout the detector writes nothing; after
+ *    a detector timeout the affected subcarriers' outputs and info entries are left
+ *    unwritten, so a caller may also fill info with a sentinel (e.g. -1) before the call.
  * Inputs, outputs, layouts and results are those of rapro_receive_subframe with
  * h_out == NULL, on the caller's stream.
  */
@@ -410,6 +427,14 @@ rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, const rapro_c
                                             const rapro_c32* pilots, const rapro_c32* y_data,
                                             rapro_c32* x_eq, uint8_t* labels, float* llr,
                                             int32_t* info, rapro_stream stream);
+
+/*
+ * Status word of the allocation-free receive on the current device: enqueues a read of it
+ * on `stream` (after the calls enqueued there before), clears it if reset != 0, and waits
+ * for the stream.  *status_out: RAPRO_OK, or RAPRO_ERR_TIMEOUT if a pipeline wait of the
+ * last rapro_receive_subframe_noalloc call ran out.  Allocates nothing.
+ */
+rapro_status rapro_noalloc_status(int reset, int* status_out, rapro_stream stream);
 
 #ifdef __cplusplus
 }

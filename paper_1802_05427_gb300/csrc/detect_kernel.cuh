@@ -59,6 +59,9 @@ struct DetParams {
   float2* h_out;          // channel estimate [T][K][M][N], or null (then not written)
   int B, nfull, tail;     // block size, full blocks, tail block length
   int span, nst;          // pilot box width in subcarriers, stage ring depth
+  // Non-null: the kernel does nothing (outputs and info untouched) when this word is
+  // non-zero on entry, i.e. when the kernel before it in the stream recorded a failure.
+  const int* skip_if_set;
 };
 
 // Kernel forms: plain detection, detection with the FP64 fallback, fused receive.
@@ -208,6 +211,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   int* s_abort = reinterpret_cast<int*>(smem + 128);
   float2* stage0 = reinterpret_cast<float2*>(smem + 1024);
 
+  if (P.skip_if_set && *reinterpret_cast<const volatile int*>(P.skip_if_set) != 0) return;   // uniform per CTA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   const int t = blockIdx.y, k0 = blockIdx.x * DET_SC;

@@ -170,6 +170,7 @@ cudaError_t launch_detect_raw(const DetTiles& tiles, int T, int K, int M, int N,
   P.nchunks = (M + DET_MCH - 1) / DET_MCH;
   P.tiles = tiles;
   P.status = status;
+  P.skip_if_set = status;               // the estimator before it timed out: leave the outputs
   return run(P, h, y, x_eq, labels, llr, info, st);
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <complex>
 #include <vector>
 
 #include "rapro.h"
@@ -72,9 +73,16 @@ inline bool half_precision(const rapro_params& p) {
 void set_error(const std::string& msg);
 rapro_status cuda_fail(cudaError_t e, const char* what);
 
+// Frequency correlation r(d) of subcarriers d apart (Eq. 16, or the exponential PDP), FP64.
+std::complex<double> corr_fp64(const rapro_params& p, int d);
+
 // Host FP64 weights of one block of len subcarriers: W = R (R + s I)^-1, row-major
 // interleaved.  Returns false if R + s I is not positive definite in FP64.
 bool build_weights_fp64(const rapro_params& p, int len, std::vector<double>& w);
+// The same arithmetic into caller storage, allocating nothing: work holds
+// weights_fp64_work(len) complex doubles, w_out 2 len^2 doubles.
+constexpr size_t weights_fp64_work(int len) { return size_t(2 * len - 1) + 2 * size_t(len) * len + size_t(len); }
+bool weights_fp64_into(const rapro_params& p, int len, std::complex<double>* work, double* w_out);
 
 DetTiles make_det_tiles(int K, int D);
 

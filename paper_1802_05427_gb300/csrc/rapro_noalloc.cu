@@ -1,13 +1,13 @@
-// Allocation-free receive: rapro_receive_subframe_noalloc.
+// Allocation-free receive: rapro_receive_subframe_noalloc and rapro_noalloc_status.
 //
 // Some callers cannot allocate device memory at the moment they receive a subframe:
-// code that runs while a CUDA graph is being captured (cudaMalloc is not allowed inside a
-// capture), real-time slot loops that must never wait on an allocator (the receiver has
-// a fixed per-slot deadline), and processes whose device memory is owned by another
-// framework's pool.  For them this entry point needs no plan and allocates nothing: the
-// channel-estimate scratch that rapro_receive_subframe keeps in its plan lives here in a
-// fixed, file-scope device array instead, and the LMMSE weights travel in the kernel
-// parameters.
+// real-time slot loops that must never wait on an allocator (the receiver has a fixed
+// per-slot deadline and cudaMalloc may synchronise the device or take milliseconds),
+// processes whose device memory is owned by another framework's pool, and deployments
+// that forbid run-time allocation altogether.  For them this entry point needs no plan
+// and allocates nothing: the channel-estimate scratch that rapro_receive_subframe keeps
+// in its plan lives here in a fixed, file-scope device array instead, and the LMMSE
+// weights travel in the kernel parameters.
 //
 // The array (kNoAllocScratchBytes) is part of the library's device image: every GPU that
 // loads the library holds it until the process exits.  All calls share it and it keeps
@@ -49,68 +49,13 @@ const DeviceScratch& device_scratch(int dev) {
   return g_scratch[dev];
 }
 
-using cd = std::complex<double>;
-
-cd corr_model(const rapro_params& p, int d) {
-  const double two_pi = 6.283185307179586476925286766559;
-  if (p.pdp == RAPRO_PDP_EXP) {
-    double norm = 0.0;
-    for (int l = 0; l < p.n_taps; ++l) norm += std::exp(-l / p.tau_rms);
-    cd acc(0.0, 0.0);
-    for (int l = 0; l < p.n_taps; ++l) {
-      const double ph = -two_pi * double(l) * double(d) / double(p.n_fft);
-      acc += (std::exp(-l / p.tau_rms) / norm) * cd(std::cos(ph), std::sin(ph));
-    }
-    return acc;
-  }
-  if (d == 0) return cd(1.0, 0.0);
-  const double x = two_pi * p.L * double(d) / double(p.n_fft);
-  const cd num(1.0 - std::cos(x), std::sin(x));
-  return num / cd(0.0, x);
-}
-
-// FP64 weights W = R (R + sigma2 I)^-1 of one block of n <= LMMSE_SMALL_MAX subcarriers,
-// on the stack: Cholesky A = L L^H, X = A^-1 R by two triangular solves, W = X^H, rounded
-// to complex64 (the same operation order as the plan's builder).
+// FP64 weights of one block of n <= LMMSE_SMALL_MAX subcarriers with the plan's builder,
+// in stack storage, rounded to complex64.
 bool small_weights(const rapro_params& p, int n, float2* w) {
-  constexpr int NM = LMMSE_SMALL_MAX;
-  cd r[2 * NM - 1], L[NM * NM], X[NM * NM], y[NM];
-  for (int d = -(n - 1); d <= n - 1; ++d) r[d + n - 1] = corr_model(p, d);
-  auto R = [&](int a, int b) { return r[a - b + n - 1]; };
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j <= i; ++j) L[i * n + j] = R(i, j) + (i == j ? p.sigma2 : 0.0);
-  for (int j = 0; j < n; ++j) {
-    cd* Lj = &L[j * n];
-    double d = Lj[j].real();
-    for (int k = 0; k < j; ++k) d -= std::norm(Lj[k]);
-    if (!(d > 0.0) || !std::isfinite(d)) return false;
-    const double ljj = std::sqrt(d);
-    Lj[j] = cd(ljj, 0.0);
-    for (int i = j + 1; i < n; ++i) {
-      cd* Li = &L[i * n];
-      cd s = Li[j];
-      for (int k = 0; k < j; ++k) s -= Li[k] * std::conj(Lj[k]);
-      Li[j] = s / ljj;
-    }
-  }
-  for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < n; ++i) {
-      cd s = R(i, c);
-      const cd* Li = &L[i * n];
-      for (int k = 0; k < i; ++k) s -= Li[k] * y[k];
-      y[i] = s / Li[i].real();
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      cd s = y[i];
-      for (int k = i + 1; k < n; ++k) s -= std::conj(L[k * n + i]) * X[k * n + c];
-      X[i * n + c] = s / L[i * n + i].real();
-    }
-  }
-  for (int a = 0; a < n; ++a)
-    for (int b = 0; b < n; ++b) {
-      const cd v = std::conj(X[b * n + a]);
-      w[a * n + b] = make_float2(float(v.real()), float(v.imag()));
-    }
+  std::complex<double> work[weights_fp64_work(LMMSE_SMALL_MAX)];
+  double wd[2 * LMMSE_SMALL_MAX * LMMSE_SMALL_MAX];
+  if (!weights_fp64_into(p, n, work, wd)) return false;
+  for (int e = 0; e < n * n; ++e) w[e] = make_float2(float(wd[2 * e]), float(wd[2 * e + 1]));
   return true;
 }
 
@@ -134,6 +79,8 @@ extern "C" rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, co
     return reject(RAPRO_ERR_INVALID_ARG, "y_pilot, pilots, y_data and x_eq must not be NULL");
   if (p->pilot_layout != RAPRO_PILOT_ORTHOGONAL)
     return reject(RAPRO_ERR_UNSUPPORTED, "the allocation-free receive reads the orthogonal pilot layout only");
+  if (half_precision(*p))
+    return reject(RAPRO_ERR_UNSUPPORTED, "the allocation-free receive runs the FP32 path only (precision = FP32)");
   if (p->subblock > LMMSE_SMALL_MAX)
     return reject(RAPRO_ERR_UNSUPPORTED, "the allocation-free receive needs subblock <= 32");
   const int T = p->n_pilot_sym, D = p->n_sym / p->n_pilot_sym - 1;
@@ -155,6 +102,8 @@ extern "C" rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, co
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // The status word only has to start at zero; the estimate is fully rewritten below.
+  // The detector reads it on entry and leaves every output untouched if the estimator
+  // recorded a timeout (its rows of the scratch would hold the previous call's estimate).
   if ((e = cudaMemsetAsync(ds.status, 0, sizeof(int), st)) != cudaSuccess)
     return cuda_fail(e, "clear status word");
   const float2* yp = reinterpret_cast<const float2*>(y_pilot);
@@ -167,5 +116,24 @@ extern "C" rapro_status rapro_receive_subframe_noalloc(const rapro_params* p, co
                         reinterpret_cast<const float2*>(y_data), reinterpret_cast<float2*>(x_eq), labels, llr,
                         info, st);
   if (e != cudaSuccess) return cuda_fail(e, "detection kernel launch");
+  return RAPRO_OK;
+}
+
+extern "C" rapro_status rapro_noalloc_status(int reset, int* status_out, rapro_stream stream) {
+  if (!status_out) return reject(RAPRO_ERR_INVALID_ARG, "status_out must not be NULL");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return reject(RAPRO_ERR_INVALID_ARG, "device index out of range");
+  const DeviceScratch& ds = device_scratch(dev);
+  if (ds.err != cudaSuccess) return cuda_fail(ds.err, "allocation-free receive set-up");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int v = 0;
+  if ((e = cudaMemcpyAsync(&v, ds.status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "read status word");
+  if (reset && (e = cudaMemsetAsync(ds.status, 0, sizeof(int), st)) != cudaSuccess)
+    return cuda_fail(e, "clear status word");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  *status_out = v;
   return RAPRO_OK;
 }

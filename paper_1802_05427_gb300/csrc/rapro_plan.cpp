@@ -30,7 +30,7 @@ rapro_status cuda_fail(cudaError_t e, const char* what) {
 using cd = std::complex<double>;
 
 // Frequency correlation r(d) between subcarriers d apart (Eq. 16 or the exponential PDP).
-static cd corr(const rapro_params& p, int d) {
+cd corr_fp64(const rapro_params& p, int d) {
   const double two_pi = 6.283185307179586476925286766559;
   if (p.pdp == RAPRO_PDP_EXP) {
     double norm = 0.0;
@@ -49,14 +49,16 @@ static cd corr(const rapro_params& p, int d) {
   return num / cd(0.0, x);
 }
 
-bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out) {
-  // r(d) for d in (-n, n)
-  std::vector<cd> r(2 * n - 1);
-  for (int d = -(n - 1); d <= n - 1; ++d) r[d + n - 1] = corr(p, d);
+bool weights_fp64_into(const rapro_params& p, int n, std::complex<double>* work, double* w_out) {
+  // work: r(d) for d in (-n, n), then L, X (n x n each), then y (n)
+  cd* r = work;
+  cd* L = r + (2 * n - 1);
+  cd* X = L + size_t(n) * n;
+  cd* y = X + size_t(n) * n;
+  for (int d = -(n - 1); d <= n - 1; ++d) r[d + n - 1] = corr_fp64(p, d);
   auto R = [&](int a, int b) { return r[a - b + n - 1]; };
 
   // A = R + sigma2 I, Cholesky in place (lower triangle), column-major access by rows.
-  std::vector<cd> L(size_t(n) * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j <= i; ++j) L[size_t(i) * n + j] = R(i, j) + (i == j ? p.sigma2 : 0.0);
   for (int j = 0; j < n; ++j) {
@@ -74,7 +76,6 @@ bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out
     }
   }
   // X = A^-1 R column by column (L y = r_col, L^H x = y); then W = X^H.
-  std::vector<cd> X(size_t(n) * n), y(n);
   for (int c = 0; c < n; ++c) {
     for (int i = 0; i < n; ++i) {
       cd s = R(i, c);
@@ -88,7 +89,6 @@ bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out
       X[size_t(i) * n + c] = s / L[size_t(i) * n + i].real();
     }
   }
-  w_out.assign(size_t(2) * n * n, 0.0);
   for (int a = 0; a < n; ++a)
     for (int b = 0; b < n; ++b) {
       const cd v = std::conj(X[size_t(b) * n + a]);   // W[a][b] = conj(X[b][a])
@@ -96,6 +96,12 @@ bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out
       w_out[2 * (size_t(a) * n + b) + 1] = v.imag();
     }
   return true;
+}
+
+bool build_weights_fp64(const rapro_params& p, int n, std::vector<double>& w_out) {
+  std::vector<cd> work(weights_fp64_work(n));
+  w_out.assign(size_t(2) * n * n, 0.0);
+  return weights_fp64_into(p, n, work.data(), w_out.data());
 }
 
 int comb_window(const rapro_params& p) {
@@ -112,7 +118,7 @@ bool build_comb_weights_fp64(const rapro_params& p, std::vector<double>& w_out) 
   const int sets = sw ? p.K : 1;
   std::vector<cd> L(size_t(Q) * Q), X(size_t(Q) * Q), y(Q);
   for (int i = 0; i < Q; ++i)
-    for (int j = 0; j <= i; ++j) L[size_t(i) * Q + j] = corr(p, (i - j) * S) + (i == j ? p.sigma2 : 0.0);
+    for (int j = 0; j <= i; ++j) L[size_t(i) * Q + j] = corr_fp64(p, (i - j) * S) + (i == j ? p.sigma2 : 0.0);
   for (int j = 0; j < Q; ++j) {
     cd* Lj = &L[size_t(j) * Q];
     double d = Lj[j].real();
@@ -134,7 +140,7 @@ bool build_comb_weights_fp64(const rapro_params& p, std::vector<double>& w_out) 
       // column c of R_o^H: conj(R_o[c][i]) over i; solve L y = col, L^H x = y.
       for (int c = 0; c < Q; ++c) {
         for (int i = 0; i < Q; ++i) {
-          cd s = std::conj(corr(p, off(c, i)));
+          cd s = std::conj(corr_fp64(p, off(c, i)));
           const cd* Li = &L[size_t(i) * Q];
           for (int m = 0; m < i; ++m) s -= Li[m] * y[m];
           y[i] = s / Li[i].real();
@@ -319,7 +325,7 @@ rapro_status rapro_weight_grad_host(const rapro_params* p, const double* g_w_mai
     std::vector<cd> R(size_t(n) * n), dR(size_t(n) * n), L(size_t(n) * n), Ai(size_t(n) * n), y(n);
     for (int a = 0; a < n; ++a)
       for (int b = 0; b < n; ++b) {
-        R[size_t(a) * n + b] = corr(*p, a - b);
+        R[size_t(a) * n + b] = corr_fp64(*p, a - b);
         dR[size_t(a) * n + b] = dcorr(a - b);
       }
     for (int i = 0; i < n; ++i)

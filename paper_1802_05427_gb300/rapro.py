@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         "rapro_receive_subframe": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
         "rapro_receive_subframe_noalloc": ([ctypes.POINTER(RaproParams), _P, _P, _P, _P, _P, _P, _P, _P],
                                            ctypes.c_int),
+        "rapro_noalloc_status": ([ctypes.c_int, _P, _P], ctypes.c_int),
+        "rapro_measure_ffma_peak": ([ctypes.c_int, _P, _P, _P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -419,6 +421,21 @@ def rapro_receive_subframe_noalloc(params: RaproParams, y_pilot, pilots, y_data,
         _ptr(y_data, (T * D, M, N), c64, "y_data"), _ptr(x_eq, (T * D, K, N), c64, "x_eq"),
         _ptr(labels, (T * D, K, N), torch.uint8, "labels"), _ptr(llr, (T * D, K, N, q), torch.float32, "llr"),
         _ptr(info, (T, N), torch.int32, "info"), _stream(stream)), "rapro_receive_subframe_noalloc")
+
+
+def rapro_noalloc_status(reset: bool = False, stream=None) -> int:
+    """Status word of the allocation-free receive on the current device (0 or RAPRO_ERR_TIMEOUT)."""
+    v = ctypes.c_int(-1)
+    _check(lib().rapro_noalloc_status(int(reset), ctypes.byref(v), _stream(stream)), "rapro_noalloc_status")
+    return v.value
+
+
+def rapro_measure_ffma_peak(trips: int = 50000, stream=None) -> tuple:
+    """(TFLOP/s, ms) of the library's FP32 FMA-chain probe on the current device."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().rapro_measure_ffma_peak(int(trips), ctypes.byref(tf), ctypes.byref(ms), _stream(stream)),
+           "rapro_measure_ffma_peak")
+    return tf.value, ms.value
 
 
 class Receiver:

@@ -66,7 +66,7 @@ def test_roofline_rows_pick_the_binding_unit():
     sh = synth.PAPER_SCALE
     hbm = 6693.5
     tc_peak = bench.tf32x3_peak()[0]
-    assert 300.0 < tc_peak < 340.0          # 1960.2 x 1.1 / 2.25 / 3 with the committed peaks
+    assert 300.0 < tc_peak < 340.0          # measured BF16 burst x 1.1 / 2.25 / 3
     a12 = bench.algorithmic(sh, 12)["ls_lmmse"]
     r = bench.roof_row(a12, 19.2, hbm, True)
     assert r["bound"] == "hbm" and abs(r["frac"] - a12["bytes"] / 19.2e-6 / 1e9 / hbm) < 1e-12
@@ -76,5 +76,16 @@ def test_roofline_rows_pick_the_binding_unit():
     assert abs(r["frac"] - a1200["flops"] / 258.7e-6 / 1e12 / tc_peak) < 1e-12
     r = bench.roof_row(a1200, 258.7, hbm, False)  # the same work on the FP32 cores
     assert r["bound"] == "alu" and r["peak"] == bench.ALU_PEAK_TFLOPS
+    r = bench.roof_row(a1200, 258.7, hbm, False, 61.5)   # against a measured FMA peak
+    assert r["bound"] == "alu" and r["peak"] == 61.5
     d = bench.algorithmic(sh, 12)["detect"]
     assert bench.roof_row(d, 24.4, hbm, False)["bound"] == "hbm"
+
+
+def test_timed_region_holds_exactly_the_requested_steps():
+    """The timed graphs add up to --steps at any count (pipelined pieces, no serial tail)."""
+    for k in (1, 3, 20, 24, 1023, 1024, 1025, 4000):
+        pieces = bench.timed_pieces(k)
+        assert sum(pieces) == k and all(0 < p <= bench.MAX_GRAPH_STEPS for p in pieces)
+    assert bench.timed_pieces(20) == [20]
+    assert bench.timed_pieces(0) == []

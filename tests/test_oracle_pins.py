@@ -424,6 +424,53 @@ def test_boundary_margin_units():
     assert O.boundary_margin(np.array([0.0 + 0.5j]), 2)[0] == 0.0
 
 
+# Off-lattice points in lattice units (levels on the odd integers, d_min / 2 = 1), with the
+# distance to the nearest decision boundary worked out by hand.  Boundaries per dimension:
+# QPSK {0}; 16-QAM {-2, 0, 2}; 64-QAM {-6, -4, -2, 0, 2, 4, 6}.  Each row: (I, Q, margin).
+_MARGIN_CASES = {
+    2: [(0.3, -0.8, 0.3), (-2.0, 1.5, 1.5), (0.9, 0.05, 0.05)],
+    4: [(0.3, 2.9, 0.3),          # I 0.3 from 0; Q 0.9 from 2
+        (-1.6, 0.55, 0.4),        # I 0.4 from -2; Q 0.55 from 0
+        (3.8, -3.5, 1.5),         # outer cell: I 1.8 from 2, Q 1.5 from -2
+        (0.05, -1.0, 0.05),       # the interior boundary at 0 decides it (else 1.0)
+        (2.25, 1.1, 0.25),        # I 0.25 from 2; Q 0.9 from 2
+        (-1.0, -0.2, 0.2)],       # Q 0.2 from 0 (else 1.0, from I)
+    6: [(0.1, 6.9, 0.1),          # I 0.1 from 0; Q 0.9 from 6
+        (-4.7, 3.2, 0.7),         # I 0.7 from -4; Q 0.8 from 4
+        (5.35, -2.6, 0.6),        # I 0.65 from 6; Q 0.6 from -2
+        (-9.0, -0.45, 0.45),      # I 3 from -6; Q 0.45 from 0
+        (3.05, 1.02, 0.95),       # I 0.95 from 4; Q 0.98 from 2
+        (-0.3, 5.0, 0.3)],        # I 0.3 from 0 (else 1.0, from Q's 4 and 6)
+}
+
+
+def _margin_cases(q):
+    scale = np.sqrt(2.0 * (4 ** (q // 2) - 1) / 3.0)
+    c = np.array(_MARGIN_CASES[q])
+    return (c[:, 0] + 1j * c[:, 1]) / scale, c[:, 2]
+
+
+@pytest.mark.parametrize("q", [2, 4, 6])
+def test_boundary_margin_off_lattice_by_hand(q):
+    x, want = _margin_cases(q)
+    np.testing.assert_allclose(O.boundary_margin(x, q), want, atol=1e-12)
+
+
+def test_boundary_margin_pin_rejects_a_dropped_interior_boundary():
+    """The hand-worked table fails a margin whose boundary set misses the one at 0."""
+    def margin_without_zero(xhat, q):
+        m = q // 2
+        scale = np.sqrt(2.0 * (4 ** m - 1) / 3.0)
+        bounds = np.array([b for b in range(-(1 << m) + 2, (1 << m) - 1, 2) if b != 0], dtype=float)
+        if bounds.size == 0:
+            return np.full(xhat.shape, np.inf)
+        d = [np.min(np.abs(c[..., None] * scale - bounds), axis=-1) for c in (np.real(xhat), np.imag(xhat))]
+        return np.minimum(d[0], d[1])
+    for q in (4, 6):
+        x, want = _margin_cases(q)
+        assert not np.allclose(margin_without_zero(x, q), want, atol=1e-12)
+
+
 # ------------------------------------------------------ end-to-end sanity
 def test_receive_chain_high_snr_is_error_free_and_lmmse_beats_ls():
     sh = _shape(M=16, K=4, n_sc=96, n_fft=256, n_taps=6, tau_rms=4.0, snr_db=25.0, qam_bits=4)

@@ -1,11 +1,13 @@
-"""The allocation-free receive entry point against the plan-based one (GPU).
+"""The allocation-free receive entry point against the plan-based one and the oracle (GPU).
 
 rapro_receive_subframe_noalloc serves callers that cannot allocate device memory when a
-subframe arrives (inside a CUDA graph capture, in a real-time slot loop, or under another
-framework's memory pool): it uses the library's fixed device scratch instead of a plan's
-workspace.  It must give the same results as rapro_receive_subframe with h_out == NULL,
-call after call, and refuse what does not fit its scratch.  This file is collected last
-so that a run stopping at the first failure has already run every other test.
+subframe arrives: real-time slot loops that must not wait on an allocator, processes whose
+device memory belongs to another framework's pool, and deployments that forbid run-time
+allocation.  It uses the library's fixed device scratch instead of a plan's workspace.  It
+must give the same results as rapro_receive_subframe with h_out == NULL, call after call,
+match the FP64 oracle like the plan path does, report its status word, and refuse what does
+not fit its scratch.  This file is collected last so that a run stopping at the first
+failure has already run every other test.
 """
 import ctypes
 
@@ -14,10 +16,11 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import rapro_oracle as O
 from paper_1802_05427_gb300 import _build, synth
 from paper_1802_05427_gb300 import rapro as R
 
-from _common import params_for, rel_err_per
+from _common import assert_parity, oracle_r, params_for
 
 pytestmark = pytest.mark.gpu
 
@@ -30,8 +33,7 @@ def _lib():
     torch.cuda.set_device(0)
 
 
-def _run(fn, sh, seed):
-    sf = synth.make_subframe(sh, seed=seed)
+def _run(fn, sf, sh):
     dev = torch.device("cuda", 0)
     ins = [torch.from_numpy(synth.as_c64(sf[k])).to(dev) for k in ("y_pilot", "pilots", "y_data")]
     T, D = sh.n_slots, sh.n_data_per_slot
@@ -50,14 +52,23 @@ def test_noalloc_matches_plan_receive_on_consecutive_calls(sh, B):
     params = params_for(sh, B)
     plan = R.Plan(params)
     for seed in (synth.SEED_BASE + 21, synth.SEED_BASE + 22):      # two calls in a row
+        sf = synth.make_subframe(sh, seed=seed)
         ref = _run(lambda yp, p, yd, x, lab, llr, info: R.rapro_receive_subframe(plan, yp, p, yd, x, lab, llr, info),
-                   sh, seed)
+                   sf, sh)
         got = _run(lambda yp, p, yd, x, lab, llr, info:
-                   R.rapro_receive_subframe_noalloc(params, yp, p, yd, x, lab, llr, info), sh, seed)
-        assert rel_err_per(got[0], ref[0].astype(np.complex128), axes=(2,)).max() <= 1e-5
+                   R.rapro_receive_subframe_noalloc(params, yp, p, yd, x, lab, llr, info), sf, sh)
+        assert_parity(got[0], ref[0], (2,), 1e-5, what="x_eq vs plan path")
         np.testing.assert_array_equal(got[1], ref[1])
         np.testing.assert_allclose(got[2], ref[2], rtol=1e-4, atol=1e-3)
         np.testing.assert_array_equal(got[3], np.zeros_like(got[3]))
+        assert R.rapro_noalloc_status(reset=True) == R.RAPRO_OK
+        # and against the FP64 oracle on the same complex64 inputs
+        c = {k: synth.as_c64(sf[k]).astype(np.complex128) for k in ("y_pilot", "pilots", "y_data")}
+        o = O.receive_subframe(c["y_pilot"], c["pilots"], c["y_data"], B=B, sigma2=sh.sigma2, r=oracle_r(sh),
+                               n_data_per_slot=sh.n_data_per_slot, q=sh.qam_bits)
+        assert_parity(got[0], o["x_eq"], (2,), 1e-5, what="x_eq vs oracle")
+        safe = O.boundary_margin(o["xhat"], sh.qam_bits) > 1e-4
+        np.testing.assert_array_equal(got[1][safe], o["labels"][safe])
     plan.close()
 
 
@@ -70,3 +81,9 @@ def test_noalloc_rejects_what_does_not_fit():
     wide = params_for(synth.PAPER_SCALE, 48)
     assert lib.rapro_receive_subframe_noalloc(ctypes.byref(wide), 8, 8, 8, 8, None, None, None, None) == \
         R.RAPRO_ERR_UNSUPPORTED
+    half = params_for(synth.PAPER_SCALE, 12)
+    half.precision = R.RAPRO_PREC_BF16
+    assert lib.rapro_receive_subframe_noalloc(ctypes.byref(half), 8, 8, 8, 8, None, None, None, None) == \
+        R.RAPRO_ERR_UNSUPPORTED
+    assert "FP32" in lib.rapro_last_error().decode()
+    assert lib.rapro_noalloc_status(0, None, None) == R.RAPRO_ERR_INVALID_ARG
