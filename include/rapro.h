@@ -382,6 +382,20 @@ rapro_status rapro_weight_grad_host(const rapro_params* p, const double* g_w_mai
                                     double* grad_out);
 
 /*
+ * Steps a4 + a5 on the tensor cores with 16-bit operands (the precision form's Gram, Eq. 22):
+ * per (slot t, subcarrier k) with H_k = h[t][:, :, k] (K users x M antennas) and Y_k the
+ * slot's D data symbols at subcarrier k,
+ *   gram[t][k][s][c] = (H_k^H H_k + sigma2 I)[s][c]   for c < K,
+ *   gram[t][k][s][K + n] = (H_k^H Y_k)[s][n]           for n < D,
+ * layout [T][n_sc][K][K + D] complex, caller-owned device memory.  h and y_data are rounded
+ * to BF16 (fp16 == 0) or FP16 (fp16 != 0), the products accumulate in FP32 (tcgen05,
+ * kind::f16).  Needs 16-byte aligned h and y_data and an even n_sc (RAPRO_ERR_UNSUPPORTED
+ * otherwise) and the orthogonal pilot layout's plan shapes.
+ */
+rapro_status rapro_gram_tc(const rapro_plan* plan, const rapro_c32* h, const rapro_c32* y_data, rapro_c32* gram,
+                           int fp16, rapro_stream stream);
+
+/*
  * Measurement utility (not a step of the receive path): the device's FP32 FMA rate.
  * Launches a full-occupancy grid (8 CTAs of 256 threads per SM) in which every thread
  * runs 8 independent FMA recurrences for 16 x trips rounds, on `stream`, timed with CUDA

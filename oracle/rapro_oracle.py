@@ -155,6 +155,68 @@ def mmse_detect(h: np.ndarray, y_data: np.ndarray, sigma2: float, n_data_per_slo
     return x_eq, s
 
 
+def gram_matched_filter(h: np.ndarray, y_data: np.ndarray, sigma2: float, n_data_per_slot: int):
+    """The two sides of Eq. 22 per (slot, subcarrier): A = H^H H + sigma2 I and z = H^H y.
+
+    h [T][K][M][N], y_data [T*D][M][N].  Returns A [T][N][K][K] and z [T][N][K][D].
+    """
+    h = np.asarray(h, dtype=np.complex128)
+    y = np.asarray(y_data, dtype=np.complex128)
+    T, K, M, N = h.shape
+    D = n_data_per_slot
+    A = np.empty((T, N, K, K), dtype=np.complex128)
+    z = np.empty((T, N, K, D), dtype=np.complex128)
+    for t in range(T):
+        Hk = np.transpose(h[t], (2, 1, 0))                     # [N][M][K]
+        HkH = np.conj(np.transpose(Hk, (0, 2, 1)))            # [N][K][M]
+        A[t] = HkH @ Hk + sigma2 * np.eye(K)
+        z[t] = HkH @ np.transpose(y[t * D:(t + 1) * D], (2, 1, 0))
+    return A, z
+
+
+def round_half(x: np.ndarray, fmt: str) -> np.ndarray:
+    """Round every real and imaginary part to a 16-bit float, nearest, ties to even:
+    fmt "bf16" (8 significant bits, FP32 exponent range) or "fp16" (IEEE binary16).
+    Used to model the operands a 16-bit product consumes; values stay float64."""
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        return round_half(x.real, fmt) + 1j * round_half(x.imag, fmt)
+    if fmt == "fp16":
+        return x.astype(np.float32).astype(np.float16).astype(np.float64)
+    # bf16: keep the top 16 bits of the FP32 pattern, rounding the dropped 16 to nearest even
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def refined_mmse_detect(h: np.ndarray, y_data: np.ndarray, sigma2: float, n_data_per_slot: int,
+                        A_low: np.ndarray, z_low: np.ndarray):
+    """One step of iterative refinement of Eq. 22 around an approximate system.
+
+    The solve uses the approximate Gram A_low and right side z_low ([T][N][K][K], [T][N][K][D]):
+      x0 = A_low^-1 z_low,
+      r  = H^H (y - H x0) - sigma2 x0      (the residual of Eq. 22 from the given H),
+      x1 = x0 + A_low^-1 r.
+    Returns x1 [T*D][K][N] and s = sigma2 [A_low^-1]_kk [T][K][N].
+    """
+    h = np.asarray(h, dtype=np.complex128)
+    y = np.asarray(y_data, dtype=np.complex128)
+    T, K, M, N = h.shape
+    D = n_data_per_slot
+    x1 = np.empty((T * D, K, N), dtype=np.complex128)
+    s = np.empty((T, K, N), dtype=np.float64)
+    for t in range(T):
+        Hk = np.transpose(h[t], (2, 1, 0))                     # [N][M][K]
+        HkH = np.conj(np.transpose(Hk, (0, 2, 1)))            # [N][K][M]
+        Yk = np.transpose(y[t * D:(t + 1) * D], (2, 1, 0))    # [N][M][D]
+        x0 = np.linalg.solve(A_low[t], z_low[t])               # [N][K][D]
+        r = HkH @ (Yk - Hk @ x0) - sigma2 * x0
+        x = x0 + np.linalg.solve(A_low[t], r)
+        x1[t * D:(t + 1) * D] = np.transpose(x, (2, 1, 0))
+        s[t] = (sigma2 * np.real(np.diagonal(np.linalg.inv(A_low[t]), axis1=1, axis2=2))).T
+    return x1, s
+
+
 def zf_detect(h: np.ndarray, y_data: np.ndarray, n_data_per_slot: int) -> np.ndarray:
     """Eq. 18-19: x~ = (H^H H)^-1 H^H y per (slot, subcarrier), by LU."""
     x, _ = mmse_detect(h, y_data, 0.0, n_data_per_slot)

@@ -59,6 +59,8 @@ struct DetParams {
   float2* h_out;          // channel estimate [T][K][M][N], or null (then not written)
   int B, nfull, tail;     // block size, full blocks, tail block length
   int span, nst;          // pilot box width in subcarriers, stage ring depth
+  // Precision form (refine kernel): the tensor-core Gram | matched filter [T][N][K][K + D].
+  const float2* gram;
   // Non-null: the kernel does nothing (outputs and info untouched) when this word is
   // non-zero on entry, i.e. when the kernel before it in the stream recorded a failure.
   const int* skip_if_set;
@@ -187,11 +189,243 @@ __device__ __forceinline__ void demap_store(float2 xt, float s, size_t o, unsign
   }
 }
 
+// Hard Gray label alone (no LLR): the nearest level per dimension, ties to the upper level,
+// bits interleaved I, Q from the most significant one (the labels of demap_store).
+template <int MB>
+__device__ __forceinline__ unsigned char hard_label(float2 xt, float s) {
+  constexpr int NL = 1 << MB, Q = 2 * MB;
+  const float scale = (MB == 1) ? 1.41421356237309505f : (MB == 2 ? 3.16227766016837933f : 6.48074069840786023f);
+  const float g = __fdividef(1.0f, 1.0f - s) * scale;
+  const float vi = xt.x * g, vq = xt.y * g;
+  const int ui = int(fminf(fmaxf(ceilf((float(NL) - vi) * 0.5f) - 1.0f, 0.0f), float(NL - 1)));
+  const int uq = int(fminf(fmaxf(ceilf((float(NL) - vq) * 0.5f) - 1.0f, 0.0f), float(NL - 1)));
+  const int gi = ui ^ (ui >> 1), gq = uq ^ (uq >> 1);
+  int lab = 0;
+#pragma unroll
+  for (int p = 0; p < MB; ++p) {
+    lab |= ((gi >> (MB - 1 - p)) & 1) << (Q - 1 - 2 * p);
+    lab |= ((gq >> (MB - 1 - p)) & 1) << (Q - 2 - 2 * p);
+  }
+  return (unsigned char)lab;
+}
+
 }  // namespace rapro
 
 #include "fixup.cuh"
 
 namespace rapro {
+
+// Per subcarrier scl (one half-warp, lane i owns row i) of a detector tile: Cholesky of the
+// lower triangle of A in As (sigma2 included), the columns of L^-1 into As, s_i = sigma2
+// [A^-1]_ii into Ss, the first failed pivot into Is; then w = L^-1 z (z in Zs) and
+// x~ = L^-H w into Xs.  FIX also flags ill-conditioned or failed subcarriers for the FP64
+// fallback.  Layouts as in the detector's epilogue (AS = KT + 1, XS = DET_SC + 1).
+template <int KT, int DT, bool FIX>
+__device__ __forceinline__ void det_factor_solve(const int i, const int scl, const int K, const int D, const int t,
+                                                 const int k0, const int N, const DetParams& P, float2* As,
+                                                 float2* Zs, float2* Xs, float* Ss, int* Is, float2* Cb) {
+  constexpr int AS = KT + 1;
+  constexpr int XS = DET_SC + 1;
+  const bool live = i < K;                 // real user row
+  const bool row = i < KT;                 // row of the padded system
+  float2* Am = As + scl * KT * AS;
+  float2* Zm = Zs + scl * KT * DT;
+  float2* cb = Cb + scl * 32;              // two 16-entry column buffers
+  float2 ar[KT];
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    if (live && j <= i) ar[j] = Am[i * AS + j];
+    else ar[j] = make_float2((row && j == i) ? 1.f : 0.f, 0.f);   // padded rows: identity
+  }
+
+  // Cholesky, column j at a time: rows publish A[.][j] in a column buffer; every lane
+  // reads the pivot and the column from it (broadcast loads) and updates its own row.
+  float inv_l[KT];
+  int fail = 0;
+  float dmax = 0.f, dmin = 3.4e38f;        // pivots L_jj^2 of the real users
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    float2* col = cb + (j & 1) * 16;
+    if (row) col[i] = ar[j];
+    __syncwarp();
+    const float d = col[j].x;
+    const bool ok = (d > 0.0f) && (d < 3.0e38f);
+    if (!ok && fail == 0) fail = j + 1;
+    if (j < K) {
+      dmax = fmaxf(dmax, d);
+      dmin = fminf(dmin, d);
+    }
+    const float il = rsqrtf(d);                            // 1 / L_jj
+    inv_l[j] = il;
+    const float2 lij = make_float2(ar[j].x * il, ar[j].y * il);   // L[i][j] for i > j
+#pragma unroll
+    for (int l = j + 1; l < KT; ++l) {
+      const float2 a = col[l];                             // A[l][j]; L[l][j] = a * il
+      if (i >= l) {                                        // A[i][l] -= L[i][j] conj(L[l][j])
+        ar[l].x -= fmaf(lij.x, a.x, lij.y * a.y) * il;
+        ar[l].y -= fmaf(lij.y, a.x, -lij.x * a.y) * il;
+      }
+    }
+    ar[j] = (i == j) ? make_float2(d * il, 0.f) : ((i > j) ? lij : ar[j]);
+  }
+  if (row) {
+#pragma unroll
+    for (int j = 0; j < KT; ++j) Am[i * AS + j] = ar[j];   // row i of L
+  }
+  __syncwarp();
+  // Column i of L^-1 by forward substitution with pending sums: once y_j is known, every
+  // later row r gets pend[r] += L[r][j] y_j (independent updates, broadcast loads).
+  float2 yc[KT], pend[KT];
+#pragma unroll
+  for (int r = 0; r < KT; ++r) pend[r] = make_float2(0.f, 0.f);
+  float sk = 0.f;
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    const float il = inv_l[j];
+    yc[j] = (j == i) ? make_float2(il, 0.f)
+                     : ((j > i) ? make_float2(-pend[j].x * il, -pend[j].y * il) : make_float2(0.f, 0.f));
+    sk = fmaf(yc[j].x, yc[j].x, fmaf(yc[j].y, yc[j].y, sk));
+#pragma unroll
+    for (int r = j + 1; r < KT; ++r) cmac(pend[r], Am[r * AS + j], yc[j]);
+  }
+  __syncwarp();
+  if (row) {
+#pragma unroll
+    for (int j = 0; j < KT; ++j) Am[j * AS + i] = yc[j];   // L^-1[j][i]
+  }
+  if (live) Ss[i * XS + scl] = P.sigma2 * sk;
+  if (i == 0) Is[scl] = fail;
+  if (FIX && i == 0 && P.fix_count && k0 + scl < N && (fail != 0 || dmax > P.cond_limit * dmin)) {
+    const int slot = atomicAdd(P.fix_count, 1);              // (max L_jj / min L_jj)^2 <= cond(A)
+    if (slot < P.fix_cap) P.fix_list[slot] = t * N + k0 + scl;
+  }
+  __syncwarp();
+  // w_i = sum_{l <= i} L^-1[i][l] z_l (row i of L^-1 first, then the broadcast z reads).
+  float2 yrow[KT], wr[DT];
+#pragma unroll
+  for (int l = 0; l < KT; ++l) yrow[l] = live ? Am[i * AS + l] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int n = 0; n < DT; ++n) wr[n] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int l = 0; l < KT; ++l) {
+    if (l < K) {
+#pragma unroll
+      for (int n = 0; n < DT; ++n) cmac(wr[n], yrow[l], Zm[l * DT + n]);
+    }
+  }
+  __syncwarp();
+  if (live) {
+#pragma unroll
+    for (int n = 0; n < DT; ++n) Zm[i * DT + n] = wr[n];
+  }
+  __syncwarp();
+  // x~_i = sum_{j >= i} conj(L^-1[j][i]) w_j  (column i of L^-1 is still in yc).
+  float2 xr[DT];
+#pragma unroll
+  for (int n = 0; n < DT; ++n) xr[n] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    if (j < K) {
+#pragma unroll
+      for (int n = 0; n < DT; ++n) cmac_conj(xr[n], yc[j], Zm[j * DT + n]);
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int n = 0; n < DT; ++n)
+      if (n < D) Xs[(n * KT + i) * XS + scl] = xr[n];
+  }
+}
+
+// w = L^-1 r and x~ += L^-H w for subcarrier scl, with the columns of L^-1 in As (as left by
+// det_factor_solve) and the right-hand sides r in Zs (overwritten by w).
+template <int KT, int DT>
+__device__ __forceinline__ void det_solve_add(const int i, const int scl, const int K, const int D, const float2* As,
+                                              float2* Zs, float2* Xs) {
+  constexpr int AS = KT + 1;
+  constexpr int XS = DET_SC + 1;
+  const bool live = i < K;
+  const float2* Am = As + scl * KT * AS;
+  float2* Zm = Zs + scl * KT * DT;
+  float2 wr[DT];
+#pragma unroll
+  for (int n = 0; n < DT; ++n) wr[n] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int l = 0; l < KT; ++l) {
+    if (l < K && live && l <= i) {
+      const float2 a = Am[i * AS + l];                         // L^-1[i][l]
+#pragma unroll
+      for (int n = 0; n < DT; ++n) cmac(wr[n], a, Zm[l * DT + n]);
+    }
+  }
+  __syncwarp();
+  if (live) {
+#pragma unroll
+    for (int n = 0; n < DT; ++n) Zm[i * DT + n] = wr[n];
+  }
+  __syncwarp();
+  float2 xr[DT];
+#pragma unroll
+  for (int n = 0; n < DT; ++n) xr[n] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < KT; ++j) {
+    if (j < K && live) {
+      const float2 c = Am[j * AS + i];                         // L^-1[j][i], zero above the diagonal
+#pragma unroll
+      for (int n = 0; n < DT; ++n) cmac_conj(xr[n], c, Zm[j * DT + n]);
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int n = 0; n < DT; ++n)
+      if (n < D) {
+        float2& x = Xs[(n * KT + i) * XS + scl];
+        x.x += xr[n].x;
+        x.y += xr[n].y;
+      }
+  }
+}
+
+// Demap the tile's x~ (Xs, with s in Ss) and store x_eq, labels and LLRs with coalesced
+// writes, all threads of the CTA.
+template <int KT, int DT>
+__device__ __forceinline__ void det_demap_store(const int t, const int k0, const int K, const int D, const int N,
+                                                const int q, const float2* Xs, const float* Ss, float2* x_eq,
+                                                unsigned char* labels, float* llr) {
+  constexpr int XS = DET_SC + 1;
+  // Thread -> subcarrier scx and a group g of (symbol, user) rows; rows advance by the
+  // group count (no division by K), and each 16-lane group writes 16 consecutive entries.
+  {
+    const int scx = threadIdx.x % DET_SC, g0 = threadIdx.x / DET_SC, G = blockDim.x / DET_SC;
+    const int kg = k0 + scx;
+    if (kg < N && g0 < G) {
+      int n = 0, k = g0;
+      while (k >= K) { k -= K; ++n; }
+      for (; n < D;) {
+        const float2 xt = Xs[(n * KT + k) * XS + scx];
+        const size_t o = (size_t(t * D + n) * K + k) * N + kg;
+        x_eq[o] = xt;
+        if (llr) {
+          const float s = Ss[k * XS + scx];
+          switch (q) {
+            case 2: demap_store<1>(xt, s, o, labels, llr); break;
+            case 4: demap_store<2>(xt, s, o, labels, llr); break;
+            default: demap_store<3>(xt, s, o, labels, llr); break;
+          }
+        } else if (labels) {
+          const float s = Ss[k * XS + scx];
+          switch (q) {
+            case 2: labels[o] = hard_label<1>(xt, s); break;
+            case 4: labels[o] = hard_label<2>(xt, s); break;
+            default: labels[o] = hard_label<3>(xt, s); break;
+          }
+        }
+        k += G;
+        while (k >= K) { k -= K; ++n; }
+      }
+    }
+  }
+}
 
 // ------------------------------------------------------------------------ kernel
 // MODE DET_FIX compiles in the FP64 fallback of the precision form (flagging and the last
@@ -575,138 +809,11 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   // (a single pass keeps the row arrays in registers).  Lane i owns row i.
   const int hw = lane >> 4, i = lane & 15;
   const int scl = warp * 2 + hw;
-  if (scl < DET_SC) {
-    const bool live = i < K;                 // real user row
-    const bool row = i < KT;                 // row of the padded system
-    float2* Am = As + scl * KT * AS;
-    float2* Zm = Zs + scl * KT * DT;
-    float2* cb = Cb + scl * 32;              // two 16-entry column buffers
-    float2 ar[KT];
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-      if (live && j <= i) ar[j] = Am[i * AS + j];
-      else ar[j] = make_float2((row && j == i) ? 1.f : 0.f, 0.f);   // padded rows: identity
-    }
-
-    // Cholesky, column j at a time: rows publish A[.][j] in a column buffer; every lane
-    // reads the pivot and the column from it (broadcast loads) and updates its own row.
-    float inv_l[KT];
-    int fail = 0;
-    float dmax = 0.f, dmin = 3.4e38f;        // pivots L_jj^2 of the real users
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-      float2* col = cb + (j & 1) * 16;
-      if (row) col[i] = ar[j];
-      __syncwarp();
-      const float d = col[j].x;
-      const bool ok = (d > 0.0f) && (d < 3.0e38f);
-      if (!ok && fail == 0) fail = j + 1;
-      if (j < K) {
-        dmax = fmaxf(dmax, d);
-        dmin = fminf(dmin, d);
-      }
-      const float il = rsqrtf(d);                            // 1 / L_jj
-      inv_l[j] = il;
-      const float2 lij = make_float2(ar[j].x * il, ar[j].y * il);   // L[i][j] for i > j
-#pragma unroll
-      for (int l = j + 1; l < KT; ++l) {
-        const float2 a = col[l];                             // A[l][j]; L[l][j] = a * il
-        if (i >= l) {                                        // A[i][l] -= L[i][j] conj(L[l][j])
-          ar[l].x -= fmaf(lij.x, a.x, lij.y * a.y) * il;
-          ar[l].y -= fmaf(lij.y, a.x, -lij.x * a.y) * il;
-        }
-      }
-      ar[j] = (i == j) ? make_float2(d * il, 0.f) : ((i > j) ? lij : ar[j]);
-    }
-    if (row) {
-#pragma unroll
-      for (int j = 0; j < KT; ++j) Am[i * AS + j] = ar[j];   // row i of L
-    }
-    __syncwarp();
-    // Column i of L^-1 by forward substitution with pending sums: once y_j is known, every
-    // later row r gets pend[r] += L[r][j] y_j (independent updates, broadcast loads).
-    float2 yc[KT], pend[KT];
-#pragma unroll
-    for (int r = 0; r < KT; ++r) pend[r] = make_float2(0.f, 0.f);
-    float sk = 0.f;
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-      const float il = inv_l[j];
-      yc[j] = (j == i) ? make_float2(il, 0.f)
-                       : ((j > i) ? make_float2(-pend[j].x * il, -pend[j].y * il) : make_float2(0.f, 0.f));
-      sk = fmaf(yc[j].x, yc[j].x, fmaf(yc[j].y, yc[j].y, sk));
-#pragma unroll
-      for (int r = j + 1; r < KT; ++r) cmac(pend[r], Am[r * AS + j], yc[j]);
-    }
-    __syncwarp();
-    if (row) {
-#pragma unroll
-      for (int j = 0; j < KT; ++j) Am[j * AS + i] = yc[j];   // L^-1[j][i]
-    }
-    if (live) Ss[i * XS + scl] = P.sigma2 * sk;
-    if (i == 0) Is[scl] = fail;
-    if (FIX && i == 0 && P.fix_count && k0 + scl < N && (fail != 0 || dmax > P.cond_limit * dmin)) {
-      const int slot = atomicAdd(P.fix_count, 1);              // (max L_jj / min L_jj)^2 <= cond(A)
-      if (slot < P.fix_cap) P.fix_list[slot] = t * N + k0 + scl;
-    }
-    __syncwarp();
-    // w_i = sum_{l <= i} L^-1[i][l] z_l (row i of L^-1 first, then the broadcast z reads).
-    float2 yrow[KT], wr[DT];
-#pragma unroll
-    for (int l = 0; l < KT; ++l) yrow[l] = live ? Am[i * AS + l] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int n = 0; n < DT; ++n) wr[n] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int l = 0; l < KT; ++l) {
-      if (l < K) {
-#pragma unroll
-        for (int n = 0; n < DT; ++n) cmac(wr[n], yrow[l], Zm[l * DT + n]);
-      }
-    }
-    __syncwarp();
-    if (live) {
-#pragma unroll
-      for (int n = 0; n < DT; ++n) Zm[i * DT + n] = wr[n];
-    }
-    __syncwarp();
-    // x~_i = sum_{j >= i} conj(L^-1[j][i]) w_j  (column i of L^-1 is still in yc).
-    float2 xr[DT];
-#pragma unroll
-    for (int n = 0; n < DT; ++n) xr[n] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < KT; ++j) {
-      if (j < K) {
-#pragma unroll
-        for (int n = 0; n < DT; ++n) cmac_conj(xr[n], yc[j], Zm[j * DT + n]);
-      }
-    }
-    if (live) {
-#pragma unroll
-      for (int n = 0; n < DT; ++n)
-        if (n < D) Xs[(n * KT + i) * XS + scl] = xr[n];
-    }
-  }
+  if (scl < DET_SC) det_factor_solve<KT, DT, FIX>(i, scl, K, D, t, k0, N, P, As, Zs, Xs, Ss, Is, Cb);
   __syncthreads();
 
   // ------------------------------------------------ demap and coalesced stores
-  const int total = D * K * DET_SC;
-#pragma unroll 2
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int scx = idx % DET_SC, k = (idx / DET_SC) % K, n = idx / (DET_SC * K);
-    const int kg = k0 + scx;
-    if (kg >= N) continue;
-    const float2 xt = Xs[(n * KT + k) * XS + scx];
-    const size_t o = (size_t(t * D + n) * K + k) * N + kg;
-    x_eq[o] = xt;
-    if (labels || llr) {
-      const float s = Ss[k * XS + scx];
-      switch (P.q) {
-        case 2: demap_store<1>(xt, s, o, labels, llr); break;
-        case 4: demap_store<2>(xt, s, o, labels, llr); break;
-        default: demap_store<3>(xt, s, o, labels, llr); break;
-      }
-    }
-  }
+  det_demap_store<KT, DT>(t, k0, K, D, N, P.q, Xs, Ss, x_eq, labels, llr);
   if (info && threadIdx.x < DET_SC && k0 + threadIdx.x < N) info[size_t(t) * N + k0 + threadIdx.x] = Is[threadIdx.x];
   finish_fix(true);
 }

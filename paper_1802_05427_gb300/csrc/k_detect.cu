@@ -21,8 +21,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 3-D map over complex64 data [depth][M][N] with boxes of box_x x DET_MCH x box_z.
-static bool encode_map(CUtensorMap* m, const void* base, int N, int M, int depth, int box_z,
-                       int box_x = DET_SC) {
+bool encode_cx_map(CUtensorMap* m, const void* base, int N, int M, int depth, int box_z, int box_x) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[3] = {cuuint64_t(N), cuuint64_t(M), cuuint64_t(depth)};
@@ -32,6 +31,11 @@ static bool encode_map(CUtensorMap* m, const void* base, int N, int M, int depth
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool encode_map(CUtensorMap* m, const void* base, int N, int M, int depth, int box_z,
+                       int box_x = DET_SC) {
+  return encode_cx_map(m, base, N, M, depth, box_z, box_x);
 }
 
 static int padded_users(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16; }
@@ -109,6 +113,9 @@ static cudaError_t run(DetParams P, const float2* h, const float2* y, float2* x_
 
 cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
                           unsigned char* labels, float* llr, int* info, cudaStream_t st) {
+  // Precision form: Gram on the tensor cores, one FP32 refinement step (shape rules of the
+  // tensor-core Gram; other inputs take the FP32 detector with the FP64 fallback).
+  if (half_precision(pl.p) && refine_ok(pl, h, y)) return launch_detect_refine(pl, h, y, x_eq, labels, llr, info, st);
   DetParams P{};
   P.T = pl.T; P.K = pl.p.K; P.M = pl.p.M; P.N = pl.p.n_sc; P.D = pl.D; P.q = pl.q;
   P.sigma2 = float(pl.p.sigma2);

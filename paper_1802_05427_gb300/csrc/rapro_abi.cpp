@@ -154,6 +154,22 @@ rapro_status rapro_mmse_detect(const rapro_plan* plan, const rapro_c32* h, const
                   "detection kernel launch");
 }
 
+rapro_status rapro_gram_tc(const rapro_plan* plan, const rapro_c32* h, const rapro_c32* y_data, rapro_c32* gram,
+                           int fp16, rapro_stream stream) {
+  if (!plan) return bad("plan is NULL");
+  if (!h || !y_data || !gram) return bad("h, y_data and gram must not be NULL");
+  const Plan* pl = reinterpret_cast<const Plan*>(plan);
+  rapro_status s = check_device(pl);
+  if (s == RAPRO_OK) s = orthogonal_only(pl);
+  if (s != RAPRO_OK) return s;
+  if (!gram_tc_ok(*pl, h, y_data)) {
+    set_error("the tensor-core Gram needs 16-byte aligned h and y_data and an even n_sc");
+    return RAPRO_ERR_UNSUPPORTED;
+  }
+  return launched(launch_gram_tc(*pl, f2(h), f2(y_data), f2(gram), fp16 != 0, cs(stream)),
+                  "tensor-core Gram kernel launch");
+}
+
 rapro_status rapro_receive_subframe(const rapro_plan* plan, const rapro_c32* y_pilot,
                                     const rapro_c32* pilots, const rapro_c32* y_data,
                                     rapro_c32* h_out, rapro_c32* x_eq, uint8_t* labels, float* llr,

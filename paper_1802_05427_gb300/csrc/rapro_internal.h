@@ -57,6 +57,7 @@ struct Plan {
   // raises the throughput of pipelined subframes; set by rapro_plan_tune / _set_variant.
   int est_ctas_per_sm = 1;
   int* d_fix = nullptr;            // precision form: FP64-fallback count, ticket, list [T n_sc]
+  float2* d_gram = nullptr;        // precision form: tensor-core Gram | matched filter [T][n_sc][K][K + D]
   bool comb = false;               // comb pilot layout (Sec. II)
   std::vector<float2> w_comb;      // comb weights [sets][Q][Q][Q] (3W: 1 set, S-W: K sets)
   float2* d_w_comb = nullptr;
@@ -141,6 +142,22 @@ void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out);
 bool lmmse_tcg_ok(const Plan& pl, const float2* x, const float2* out);
 cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st);
 cudaError_t prepare_lmmse_tcg(int device);
+
+// Gram and matched filter on tcgen05 with 16-bit operands (precision form): G[t][k][s][c] =
+// (H^H H + sigma2 I | H^H Y)[s][c] per (slot, subcarrier); needs 16-byte aligned h and y
+// and even n_sc (TMA boxes).
+bool gram_tc_ok(const Plan& pl, const void* h, const void* y);
+cudaError_t launch_gram_tc(const Plan& pl, const float2* h, const float2* y, float2* G, bool fp16,
+                           cudaStream_t st);
+cudaError_t prepare_gram_tc(int device);
+
+// Precision-form detection: the tensor-core Gram of 16-bit operands, its FP32 Cholesky and
+// one FP32 refinement step with the residual from h (k_refine.cu); half-precision plans
+// with gram_tc_ok inputs take it.
+bool refine_ok(const Plan& pl, const void* h, const void* y);
+cudaError_t launch_detect_refine(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
+                                 unsigned char* labels, float* llr, int* info, cudaStream_t st);
+cudaError_t prepare_refine(int device);
 
 cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, float2* x_eq,
                           unsigned char* labels, float* llr, int* info, cudaStream_t st);

@@ -453,12 +453,14 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   if ((e = prepare_estimate(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "estimator set-up"); }
   if ((e = prepare_lmmse_tc(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core estimator set-up"); }
   if ((e = prepare_lmmse_tcg(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core GEMM set-up"); }
+  if ((e = prepare_gram_tc(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "tensor-core Gram set-up"); }
+  if ((e = prepare_refine(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "refined detector set-up"); }
   if ((e = prepare_comb(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "comb estimator set-up"); }
   if ((e = prepare_adjoint(pl->device)) != cudaSuccess) { delete pl; return cuda_fail(e, "adjoint set-up"); }
   const size_t h_elems = size_t(pl->T) * p->K * p->M * p->n_sc;
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
-    cudaFree(pl->d_w_tc); cudaFree(pl->d_w_tcg); cudaFree(pl->d_w_comb); cudaFree(pl->d_fix);
+    cudaFree(pl->d_w_tc); cudaFree(pl->d_w_tcg); cudaFree(pl->d_w_comb); cudaFree(pl->d_fix); cudaFree(pl->d_gram);
     delete pl;
     return cuda_fail(err, what);
   };
@@ -483,6 +485,10 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
     if ((e = cudaMalloc(&pl->d_fix, (2 + size_t(pl->T) * p->n_sc) * sizeof(int))) != cudaSuccess)
       return fail(e, "cudaMalloc FP64-fallback list");
     if ((e = cudaMemset(pl->d_fix, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e, "cudaMemset FP64-fallback count");
+    // The tensor-core Gram and matched filter of the refined detector: [T][n_sc][K][K + D].
+    if (!pl->comb &&
+        (e = cudaMalloc(&pl->d_gram, size_t(pl->T) * p->n_sc * p->K * (p->K + pl->D) * sizeof(float2))) != cudaSuccess)
+      return fail(e, "cudaMalloc Gram workspace");
   }
   if (!pl->comb && lmmse_tc_shape_ok(*pl)) {
     std::vector<unsigned char> wtc;
@@ -515,6 +521,7 @@ rapro_status rapro_plan_destroy(rapro_plan* plan) {
   cudaFree(pl->d_w_tcg);
   cudaFree(pl->d_w_comb);
   cudaFree(pl->d_fix);
+  cudaFree(pl->d_gram);
   delete pl;
   return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, "rapro_plan_destroy");
 }

@@ -9,6 +9,10 @@
 
 namespace rapro {
 
+// Host: 3-D TMA map over complex64 data [depth][M][N] (subcarrier fastest) with boxes of
+// box_x subcarriers x 8 antennas x box_z rows; false if the driver rejects it.
+bool encode_cx_map(CUtensorMap* m, const void* base, int N, int M, int depth, int box_z, int box_x);
+
 // A wait gives up after this many try_wait rounds; each round suspends the thread until the
 // phase completes or at most kSuspendHintNs pass, so a waiting warp takes few issue slots
 // from the warps (and co-resident CTAs) that work, and a wait ends within about 2 s.
@@ -164,6 +168,13 @@ __device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(-a.y, b.y, acc.x);
   acc.y = fmaf(a.x, b.y, acc.y);
   acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+__device__ __forceinline__ void cmac_conj_rev(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  acc.y = fmaf(-a.x, b.y, acc.y);
 }
 // acc += conj(a) * b
 __device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {

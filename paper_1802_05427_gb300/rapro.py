@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         "rapro_receive_subframe_noalloc": ([ctypes.POINTER(RaproParams), _P, _P, _P, _P, _P, _P, _P, _P],
                                            ctypes.c_int),
         "rapro_noalloc_status": ([ctypes.c_int, _P, _P], ctypes.c_int),
+        "rapro_gram_tc": ([_P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
         "rapro_measure_ffma_peak": ([ctypes.c_int, _P, _P, _P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -421,6 +422,17 @@ def rapro_receive_subframe_noalloc(params: RaproParams, y_pilot, pilots, y_data,
         _ptr(y_data, (T * D, M, N), c64, "y_data"), _ptr(x_eq, (T * D, K, N), c64, "x_eq"),
         _ptr(labels, (T * D, K, N), torch.uint8, "labels"), _ptr(llr, (T * D, K, N, q), torch.float32, "llr"),
         _ptr(info, (T, N), torch.int32, "info"), _stream(stream)), "rapro_receive_subframe_noalloc")
+
+
+def rapro_gram_tc(plan: Plan, h, y_data, gram, fp16: bool = False, stream=None) -> None:
+    """Gram and matched filter on the tensor cores (16-bit operands): gram [T][n_sc][K][K + D]."""
+    import torch
+    s = plan.shapes()
+    c64 = torch.complex64
+    T, K, N, D = plan.T, plan.params.K, plan.params.n_sc, plan.D
+    _check(lib().rapro_gram_tc(plan.handle, _ptr(h, s["h"], c64, "h"), _ptr(y_data, s["y_data"], c64, "y_data"),
+                               _ptr(gram, (T, N, K, K + D), c64, "gram"), int(bool(fp16)), _stream(stream)),
+           "rapro_gram_tc")
 
 
 def rapro_noalloc_status(reset: bool = False, stream=None) -> int:
