@@ -382,6 +382,18 @@ rapro_status rapro_weight_grad_host(const rapro_params* p, const double* g_w_mai
                                     double* grad_out);
 
 /*
+ * Diagnostics of the device-side timeout path (not for production use).  wait_rounds > 0
+ * limits each wait between the FP32 detector's TMA load producer and its consumers to that
+ * many bounded try-wait rounds (each suspends at most 2 us; 0 restores the default limit of
+ * about 2 s); stall_producer != 0 makes the producer post no load, so that the consumers'
+ * first wait runs out.  The kernel then records RAPRO_ERR_TIMEOUT in the plan's status word
+ * (rapro_plan_device_status), writes no output and no info entry, and returns; copies in
+ * flight are always drained with the default limit.  Affects rapro_mmse_detect and
+ * rapro_receive_subframe on the TMA path of FP32 plans.  Host only.
+ */
+rapro_status rapro_plan_set_wait_test(rapro_plan* plan, int stall_producer, uint32_t wait_rounds);
+
+/*
  * Steps a4 + a5 on the tensor cores with 16-bit operands (the precision form's Gram, Eq. 22):
  * per (slot t, subcarrier k) with H_k = h[t][:, :, k] (K users x M antennas) and Y_k the
  * slot's D data symbols at subcarrier k,

@@ -61,6 +61,12 @@ struct DetParams {
   int span, nst;          // pilot box width in subcarriers, stage ring depth
   // Precision form (refine kernel): the tensor-core Gram | matched filter [T][N][K][K + D].
   const float2* gram;
+  // Diagnostics of the timeout path (rapro_plan_set_wait_test): rounds of the waits between
+  // the load producer and the consumers (0: the default limit), and a producer that posts
+  // no load, so that a consumer's wait runs out.  Draining copies in flight always waits
+  // with the default limit.
+  uint32_t wait_rounds;
+  int stall_producer;
   // Non-null: the kernel does nothing (outputs and info untouched) when this word is
   // non-zero on entry, i.e. when the kernel before it in the stream recorded a failure.
   const int* skip_if_set;
@@ -443,6 +449,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   int* s_abort = reinterpret_cast<int*>(smem + 128);
+  int* s_issued = reinterpret_cast<int*>(smem + 144);   // loads the producer issued
   float2* stage0 = reinterpret_cast<float2*>(smem + 1024);
 
   if (P.skip_if_set && *reinterpret_cast<const volatile int*>(P.skip_if_set) != 0) return;   // uniform per CTA
@@ -479,6 +486,7 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
   uint64_t* empty = bars + DET_STAGES;        // [DET_STAGES] every consumer warp is done
   if (threadIdx.x == 0) {
     *s_abort = 0;
+    *s_issued = 0;
     if (USE_TMA) {
       for (int s = 0; s < DET_STAGES; ++s) {
         mbar_init(&full[s], 1);
@@ -495,9 +503,10 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     if (lane == 0) {
       prefetch_tensormap(&map_h);
       prefetch_tensormap(&map_y);
-      for (int c = 0; c < P.nchunks; ++c) {
+      int issued = 0;
+      for (int c = 0; c < P.nchunks && !P.stall_producer; ++c) {
         const int s = c % nst;
-        if (c >= nst && !mbar_wait_bounded(&empty[s], uint32_t(c / nst - 1) & 1u)) {
+        if (c >= nst && !mbar_wait_rounds(&empty[s], uint32_t(c / nst - 1) & 1u, P.wait_rounds)) {
           atomicExch(s_abort, 1);
           break;
         }
@@ -505,7 +514,9 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
         mbar_arrive_expect_tx(&full[s], stage_tx);
         tma_load_3d(st, &map_h, &full[s], x0, c * DET_MCH, t * K);
         tma_load_3d(st + yoff, &map_y, &full[s], k0, c * DET_MCH, t * D);
+        ++issued;
       }
+      *s_issued = issued;
     }
     __syncwarp();
   }
@@ -561,13 +572,13 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
         // Every consumer warp passes the named barrier of every chunk, so a wait that ran
         // out marks the warp aborted instead of leaving the loop.
         bool ok = !aborted && !*reinterpret_cast<volatile int*>(s_abort) &&
-                  mbar_wait_bounded(&full[s], uint32_t(c / nst) & 1u);
+                  mbar_wait_rounds(&full[s], uint32_t(c / nst) & 1u, P.wait_rounds);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) {
           if (!aborted && lane == 0) atomicExch(s_abort, 1);
           aborted = true;
         }
-      } else if (!mbar_wait_bounded(&full[s], uint32_t(c / nst) & 1u)) {
+      } else if (!mbar_wait_rounds(&full[s], uint32_t(c / nst) & 1u, P.wait_rounds)) {
         atomicExch(s_abort, 1);
         break;
       }
@@ -719,7 +730,10 @@ __global__ void __launch_bounds__(det_max_threads(KT, DT), 1)
     // A pipeline wait ran out: give the copies in flight a bounded chance to land,
     // record the timeout and leave without touching the outputs.
     if (threadIdx.x == 0) {
-      for (int s = 0; s < nst; ++s) (void)mbar_wait_bounded(&full[s], 0);
+      // Load j of stage s completes phase j / nst: wait for the last one of each stage.
+      const int issued = USE_TMA ? *s_issued : 0;
+      for (int s = 0; s < nst && s < issued; ++s)
+        (void)mbar_wait_bounded(&full[s], uint32_t((issued - 1 - s) / nst) & 1u);
       atomicExch(P.status, int(RAPRO_ERR_TIMEOUT));
     }
     finish_fix(false);

@@ -122,6 +122,8 @@ cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, floa
   P.nchunks = (pl.p.M + DET_MCH - 1) / DET_MCH;
   P.tiles = pl.tiles;
   P.status = pl.d_status;
+  P.wait_rounds = pl.wait_rounds;
+  P.stall_producer = pl.stall_producer;
   if (pl.d_fix) {                       // [0] count, [1] ticket (both reset by the kernel), [2..] list
     P.fix_count = pl.d_fix;
     P.fix_ticket = pl.d_fix + 1;

@@ -198,6 +198,14 @@ rapro_status rapro_plan_set_variant(rapro_plan* plan, int est_variant, int det_s
   return RAPRO_OK;
 }
 
+rapro_status rapro_plan_set_wait_test(rapro_plan* plan, int stall_producer, uint32_t wait_rounds) {
+  if (!plan) return bad("plan is NULL");
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  pl->stall_producer = stall_producer != 0;
+  pl->wait_rounds = wait_rounds;
+  return RAPRO_OK;
+}
+
 rapro_status rapro_plan_set_receive_form(rapro_plan* plan, int form) {
   if (!plan) return bad("plan is NULL");
   if (form != RAPRO_RECV_FUSED && form != RAPRO_RECV_SPLIT) return bad("form must be a rapro_receive_form");

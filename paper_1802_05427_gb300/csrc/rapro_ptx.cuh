@@ -59,6 +59,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Wait with a caller-chosen number of rounds (0: kSpinLimit); false when they run out.
+__device__ __forceinline__ bool mbar_wait_rounds(uint64_t* bar, uint32_t parity, uint32_t rounds) {
+  const uint32_t limit = rounds ? rounds : kSpinLimit;
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // 3-D tiled TMA load of one box into shared memory, completing on the mbarrier.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
                                             int y, int z) {

@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
                                            ctypes.c_int),
         "rapro_noalloc_status": ([ctypes.c_int, _P, _P], ctypes.c_int),
         "rapro_gram_tc": ([_P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+        "rapro_plan_set_wait_test": ([_P, ctypes.c_int, ctypes.c_uint32], ctypes.c_int),
         "rapro_measure_ffma_peak": ([ctypes.c_int, _P, _P, _P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -422,6 +423,12 @@ def rapro_receive_subframe_noalloc(params: RaproParams, y_pilot, pilots, y_data,
         _ptr(y_data, (T * D, M, N), c64, "y_data"), _ptr(x_eq, (T * D, K, N), c64, "x_eq"),
         _ptr(labels, (T * D, K, N), torch.uint8, "labels"), _ptr(llr, (T * D, K, N, q), torch.float32, "llr"),
         _ptr(info, (T, N), torch.int32, "info"), _stream(stream)), "rapro_receive_subframe_noalloc")
+
+
+def rapro_plan_set_wait_test(plan: Plan, stall_producer: bool, wait_rounds: int) -> None:
+    """Diagnostics of the timeout path: short producer/consumer waits and a silent producer."""
+    _check(lib().rapro_plan_set_wait_test(plan.handle, int(bool(stall_producer)), int(wait_rounds)),
+           "rapro_plan_set_wait_test")
 
 
 def rapro_gram_tc(plan: Plan, h, y_data, gram, fp16: bool = False, stream=None) -> None:

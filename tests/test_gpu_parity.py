@@ -942,3 +942,38 @@ def test_new_entry_points_reject_bad_arguments():
     b.close()
     # the tuner needs every array
     assert R.lib().rapro_plan_tune(orth.handle, None, None, None, None, None, None) == R.RAPRO_ERR_INVALID_ARG
+
+
+def test_detector_wait_that_runs_out_reports_a_timeout_and_writes_nothing():
+    """Timeout path of the pipeline waits, made to happen without a fault: the diagnostic
+    setting gives the detector's producer/consumer waits a short limit and stops its load
+    producer, so the consumers' first wait runs out.  The kernel records RAPRO_ERR_TIMEOUT
+    in the plan's status word, writes no output or info entry and returns; the context stays
+    usable, and with the setting off the next call matches the oracle."""
+    import time
+    sh = synth.SubframeShape(M=32, K=4, n_sc=64, n_fft=128, snr_db=15.0, qam_bits=4)
+    sf, c64 = _inputs(sh, 51)
+    h_ls = O.ls_estimate(c64["y_pilot"].astype(np.complex128), c64["pilots"].astype(np.complex128))
+    h = synth.as_c64(O.subblock_lmmse(h_ls, 8, oracle_r(sh), sh.sigma2))
+    plan = R.Plan(params_for(sh, 8))
+    s = plan.shapes()
+    hd, yd = _dev(h), _dev(c64["y_data"])
+    x = torch.full(s["x_eq"], float("nan"), dtype=torch.complex64, device="cuda")
+    lab = torch.full(s["labels"], 7, dtype=torch.uint8, device="cuda")
+    info = torch.full(s["info"], -7, dtype=torch.int32, device="cuda")
+    R.rapro_plan_set_wait_test(plan, True, 64)          # <= 64 rounds of <= 2 us per wait
+    torch.cuda.synchronize()
+    t0 = time.time()
+    R.rapro_mmse_detect(plan, hd, yd, x, lab, None, info)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 1.0                       # returned after the short limit
+    assert plan.device_status(reset=True) == R.RAPRO_ERR_TIMEOUT
+    assert np.isnan(_host(x)).all() and (_host(lab) == 7).all() and (_host(info) == -7).all()
+    R.rapro_plan_set_wait_test(plan, False, 0)
+    R.rapro_mmse_detect(plan, hd, yd, x, lab, None, info)
+    assert plan.device_status() == 0
+    x_o, _ = O.mmse_detect(h.astype(np.complex128), c64["y_data"].astype(np.complex128), sh.sigma2,
+                           sh.n_data_per_slot)
+    assert_parity(_host(x), x_o, (2,), TOL, what="after the timeout")
+    assert (_host(info) == 0).all()
+    plan.close()
