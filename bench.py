@@ -267,6 +267,47 @@ def measure_ffma(R, dev, trips=50000, runs=5):
     return out
 
 
+def precision_accuracy(R, synth, dev, B, n_sub=20):
+    """NMSE of h and EVM of x~ over n_sub paper-scale subframes (64-QAM, 25 dB) for the FP32,
+    BF16 and FP16 forms, each against the true channel and transmitted symbols."""
+    import torch
+    sh = synth.SubframeShape(**{**synth.PAPER_SCALE.__dict__, "snr_db": 25.0, "qam_bits": 6})
+    forms = {"fp32": R.RAPRO_PREC_FP32, "bf16_tc": R.RAPRO_PREC_BF16, "fp16_tc": R.RAPRO_PREC_FP16}
+    plans = {}
+    for name, pv in forms.items():
+        plans[name] = R.Plan(R.make_params(M=sh.M, K=sh.K, n_sc=sh.n_sc, n_fft=sh.n_fft, subblock=B,
+                                           sigma2=sh.sigma2, qam_bits=sh.qam_bits, n_taps=sh.n_taps,
+                                           tau_rms=sh.tau_rms, precision=pv))
+    s = plans["fp32"].shapes()
+    acc = {name: [0.0, 0.0] for name in forms}
+    pow_h = pow_x = 0.0
+    x = torch.empty(s["x_eq"], dtype=torch.complex64, device=dev)
+    h = torch.empty(s["h"], dtype=torch.complex64, device=dev)
+    for i in range(n_sub):
+        sf = synth.make_subframe(sh, seed=synth.SEED_BASE + 9000 + i)
+        ins = [torch.from_numpy(synth.as_c64(sf[k])).to(dev) for k in ("y_pilot", "pilots", "y_data")]
+        H = np.transpose(sf["H"], (1, 0, 2))[None]
+        pow_h += sh.n_slots * float(np.sum(np.abs(H) ** 2))
+        pow_x += float(np.sum(np.abs(sf["x"]) ** 2))
+        for name, pl in plans.items():
+            R.rapro_receive_subframe(pl, *ins, x, h_out=h)
+            torch.cuda.synchronize()
+            acc[name][0] += float(np.sum(np.abs(h.cpu().numpy() - H) ** 2))
+            acc[name][1] += float(np.sum(np.abs(x.cpu().numpy() - sf["x"]) ** 2))
+    out = {"workload": f"{sh.M}x{sh.K}, {sh.n_sc} sc, {n_sub} subframes, 64-QAM, 25 dB, B = {B}",
+           "reference": "true channel and transmitted symbols of the generator"}
+    db = lambda v: 10.0 * np.log10(v)
+    for name, pl in plans.items():
+        assert pl.device_status() == 0
+        nmse, evm = db(acc[name][0] / pow_h), db(acc[name][1] / pow_x)
+        out[name] = {"nmse_db": nmse, "evm_db": evm, "evm_pct": 100.0 * np.sqrt(acc[name][1] / pow_x)}
+        pl.close()
+    for name in ("bf16_tc", "fp16_tc"):
+        out[name]["nmse_minus_fp32_db"] = out[name]["nmse_db"] - out["fp32"]["nmse_db"]
+        out[name]["evm_minus_fp32_db"] = out[name]["evm_db"] - out["fp32"]["evm_db"]
+    return out
+
+
 # ------------------------------------------------------------ multi-rank
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """The largest of every rank's value (a timed region ends when the slowest rank does)."""
@@ -681,16 +722,17 @@ def run_rapro(args):
                                qam_bits=sh.qam_bits, n_taps=sh.n_taps, tau_rms=sh.tau_rms, precision=pv)
             plbs = [R.Plan(pb) for _ in range(IN_FLIGHT)]
 
-            def bstep(i, det=True, stream=None):
+            def bstep(i, which="full", stream=None):
                 d, o, plb = sets[i % N_SETS], outs[i % IN_FLIGHT], plbs[i % IN_FLIGHT]
-                R.rapro_ce_ls_lmmse(plb, d["y_pilot"], d["pilots"], o["h"], stream=stream)
-                if det:
+                if which != "det":
+                    R.rapro_ce_ls_lmmse(plb, d["y_pilot"], d["pilots"], o["h"], stream=stream)
+                if which != "est":
                     R.rapro_mmse_detect(plb, o["h"], d["y_data"], o["x"], o["lab"], None, o["info"], stream=stream)
             for i in range(3):
                 bstep(i)
             torch.cuda.synchronize()
             gb = []
-            for det, pipes in ((True, IN_FLIGHT), (False, 1)):
+            for which, pipes in (("full", IN_FLIGHT), ("est", 1), ("det", 1)):
                 g = torch.cuda.CUDAGraph()
                 st = torch.cuda.Stream()
                 side = [torch.cuda.Stream() for _ in range(pipes)]
@@ -702,7 +744,7 @@ def run_rapro(args):
                         for q in side:
                             q.wait_event(fork)
                         for i in range(GRAPH_STEPS):
-                            bstep(i, det, stream=side[i % pipes])
+                            bstep(i, which, stream=side[i % pipes])
                         for q in side:
                             join = torch.cuda.Event()
                             join.record(q)
@@ -711,12 +753,22 @@ def run_rapro(args):
                 gb.append(g)
             reps_b = 64 if Bp < 1200 else 4
             us_b_full, us_b_est = time_graph(gb[0], reps_b), time_graph(gb[1], reps_b)
-            prec[name] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est}
+            us_b_det = time_graph(gb[2], reps_b)
+            prec[name] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est,
+                          "detector_us": us_b_det,
+                          "detector": "tensor-core Gram of 16-bit operands + FP32 Cholesky + one FP32 refinement step"}
             if Bp == B:
                 prec[name]["estimator_hbm_frac"] = alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)
             for plb in plbs:
                 assert plb.device_status() == 0
                 plb.close()
+
+    # The precision workload (128 x 12 x 1200, 20 subframes, 64-QAM, 25 dB, B = 12): channel
+    # NMSE and EVM of the equalised symbols of the FP32 path and of each 16-bit form, against
+    # the generator's true channel and transmitted symbols (the tests tie the FP32 path to the
+    # FP64 oracle at 1e-5, so the FP32 figures stand for the oracle's).
+    if want("precision") and rank == 0 and world == 1 and B % 2 == 0 and B <= 16 and sh.n_sc % B == 0:
+        prec["accuracy_20_subframes_64qam_25db"] = precision_accuracy(R, synth, dev, B)
 
     # differentiable receive: forward + adjoint per subframe, and an Adam fit of (sigma2, tau)
     diff = {}

@@ -386,18 +386,29 @@ static cudaError_t launch_tc(const Plan& pl, const float2* y, const float2* pil,
   const int B = pl.B, M = pl.p.M, N = pl.p.n_sc, R = pl.T * pl.p.K * pl.p.M;
   const long long n_rb = (long long)R * (N / B);
   const int n_tiles = int((n_rb + TC_ROWS - 1) / TC_ROWS);
-  int dev = 0, sms = 148, smem_sm = 0, reserved = 0;
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  // SM count, shared memory per SM, reserved shared memory and this kernel's registers, read
+  // once per device (the first launch may not be inside a stream capture).
+  struct Attrs { int sms = 148, smem_sm = 0, reserved = 0, regs = 1; };
+  static Attrs attrs[64];
+  static std::once_flag once[64];
+  std::call_once(once[dev], [dev] {
+    Attrs& a = attrs[dev];
+    cudaDeviceGetAttribute(&a.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&a.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&a.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, lmmse_tc_kernel<KR, OP>) == cudaSuccess) a.regs = std::max(fa.numRegs, 1);
+  });
+  const Attrs& at = attrs[dev];
+  const int sms = at.sms;
   const size_t smem = tc_smem_bytes<KR, OP>(B);
   // Resident CTAs per SM: shared memory, threads (2048 per SM), registers (64 K, allocated
   // per warp in units of 8 per thread) and tensor memory (512 columns).
-  cudaFuncAttributes fa{};
-  cudaFuncGetAttributes(&fa, lmmse_tc_kernel<KR, OP>);
-  const int regs_warp = ((std::max(fa.numRegs, 1) + 7) / 8 * 8) * 32;
-  int per_sm = int(size_t(smem_sm) / (smem + size_t(reserved)));
+  const int regs_warp = ((at.regs + 7) / 8 * 8) * 32;
+  int per_sm = int(size_t(at.smem_sm) / (smem + size_t(at.reserved)));
   per_sm = std::max(1, std::min({per_sm, 2048 / TC_THREADS, 512 / (2 * TC_N), 65536 / (regs_warp * (TC_THREADS / 32))}));
   if (pl.est_ctas_per_sm > 0) per_sm = std::min(per_sm, pl.est_ctas_per_sm);
   const int grid = std::min(n_tiles, per_sm * sms);

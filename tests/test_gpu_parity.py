@@ -977,3 +977,49 @@ def test_detector_wait_that_runs_out_reports_a_timeout_and_writes_nothing():
     assert_parity(_host(x), x_o, (2,), TOL, what="after the timeout")
     assert (_host(info) == 0).all()
     plan.close()
+
+
+def test_autograd_with_learnable_block_weights_matches_the_oracle():
+    """The block weights of Eq. 12 as autograd parameters (tied over the full blocks, the tail's
+    own) with the detector's sigma2: loss, torch gradients of W_main, W_tail and sigma2 against
+    torch.autograd of the FP64 oracle given the same weights (FP32 adjoint: 1e-3 relative),
+    and a few Adam steps on W that lower the loss."""
+    from paper_1802_05427_gb300 import autograd as AG
+    M, K, N, nfft, B, D = 16, 4, 100, 256, 12, 3
+    sh, sf, c64 = _adj_inputs(M, K, N, nfft, B, D, seed=synth.SEED_BASE + 57)
+    tail = N % B
+    rng = np.random.default_rng(5)
+    s_e, ta = torch.tensor(sh.sigma2, dtype=torch.float64), torch.tensor(sh.tau_rms, dtype=torch.float64)
+    pert = lambda n: 0.05 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    wm0 = (G.block_weight(B, s_e, ta, sh.n_taps, sh.n_fft).numpy() + pert(B)).astype(np.complex64)
+    wt0 = (G.block_weight(tail, s_e, ta, sh.n_taps, sh.n_fft).numpy() + pert(tail)).astype(np.complex64)
+    s2_0 = 1.5 * sh.sigma2
+    batch = [dict(y_pilot=_dev(c64["y_pilot"]), pilots=_dev(c64["pilots"]), y_data=_dev(c64["y_data"]),
+                  x_ref=_dev(c64["x"]))]
+    shape = dict(M=M, K=K, n_sc=N, n_fft=nfft, subblock=B, qam_bits=sh.qam_bits, n_taps=sh.n_taps,
+                 tau_rms=sh.tau_rms, n_sym=2 * (D + 1), n_pilot_sym=2)
+    wm = torch.tensor(wm0, dtype=torch.complex128, requires_grad=True)
+    wt = torch.tensor(wt0, dtype=torch.complex128, requires_grad=True)
+    s2 = torch.tensor(s2_0, dtype=torch.float64, requires_grad=True)
+    loss = AG.symbol_mse_weights(wm, wt, s2, batch, shape)
+    loss.backward()
+    wm_o = torch.tensor(wm0, dtype=torch.complex128, requires_grad=True)
+    wt_o = torch.tensor(wt0, dtype=torch.complex128, requires_grad=True)
+    s2_o = torch.tensor(s2_0, dtype=torch.float64, requires_grad=True)
+    ins = [c64[k].astype(np.complex128) for k in ("y_pilot", "pilots", "y_data", "x")]
+    loss_o, _ = G.symbol_mse(*ins, B=B, n_taps=sh.n_taps, n_fft=nfft, n_data_per_slot=D, sigma2_est=s_e, tau=ta,
+                             sigma2_det=s2_o, weights=(wm_o, wt_o))
+    loss_o.backward()
+    assert abs(float(loss) - float(loss_o)) <= 1e-5 * float(loss_o)
+    for g, go in ((wm.grad, wm_o.grad), (wt.grad, wt_o.grad)):
+        assert torch.linalg.norm(g - go) <= 1e-3 * torch.linalg.norm(go)
+    assert abs(float(s2.grad) - float(s2_o.grad)) <= 1e-3 * abs(float(s2_o.grad))
+    # learning the weights from the pilots and known symbols lowers the loss
+    opt = torch.optim.Adam([wm, wt], lr=2e-3)
+    l0 = float(loss)
+    for _ in range(20):
+        opt.zero_grad()
+        l = AG.symbol_mse_weights(wm, wt, s2.detach(), batch, shape)
+        l.backward()
+        opt.step()
+    assert float(AG.symbol_mse_weights(wm, wt, s2.detach(), batch, shape)) < l0
