@@ -182,6 +182,9 @@ def hetero_batch(dev, n_jobs=512, seed=0x18020542 + 3, bf16=False):
                 p.precision = R.RAPRO_PREC_FP32
             n_bf16 += p.precision == R.RAPRO_PREC_BF16
         pl = R.Plan(p)
+        if p.precision != R.RAPRO_PREC_FP32:
+            # the batch workload asks for BF16 filtering; its detectors stay FP32
+            R.rapro_plan_set_detector_form(pl, R.RAPRO_DET_FP32)
         s = pl.shapes()
 
         def cn(shape):
@@ -757,6 +760,38 @@ def run_rapro(args):
             prec[name] = {"res_per_s": res_per_step / (us_b_full * 1e-6), "estimator_us": us_b_est,
                           "detector_us": us_b_det,
                           "detector": "tensor-core Gram of 16-bit operands + FP32 Cholesky + one FP32 refinement step"}
+            if Bp == B:
+                # the same plans with the FP32 detector (RAPRO_DET_FP32): the 16-bit filter alone
+                for plb in plbs:
+                    R.rapro_plan_set_detector_form(plb, R.RAPRO_DET_FP32)
+                gb[0].replay()
+                torch.cuda.synchronize()
+                for i in range(3):
+                    bstep(i)
+                torch.cuda.synchronize()
+                g32 = []
+                for which, pipes in (("full", IN_FLIGHT), ("det", 1)):
+                    g = torch.cuda.CUDAGraph()
+                    st = torch.cuda.Stream()
+                    side = [torch.cuda.Stream() for _ in range(pipes)]
+                    st.wait_stream(torch.cuda.current_stream())
+                    with torch.cuda.stream(st):
+                        with torch.cuda.graph(g, stream=st):
+                            fork = torch.cuda.Event()
+                            fork.record(st)
+                            for q in side:
+                                q.wait_event(fork)
+                            for i in range(GRAPH_STEPS):
+                                bstep(i, which, stream=side[i % pipes])
+                            for q in side:
+                                join = torch.cuda.Event()
+                                join.record(q)
+                                st.wait_event(join)
+                    torch.cuda.synchronize()
+                    g32.append(g)
+                prec[name]["fp32_detector"] = {"res_per_s": res_per_step / (time_graph(g32[0], reps_b) * 1e-6),
+                                               "detector_us": time_graph(g32[1], reps_b),
+                                               "detector": "RAPRO_DET_FP32: FP32 Gram, FP64 fallback"}
             if Bp == B:
                 prec[name]["estimator_hbm_frac"] = alg["ls_lmmse"]["bytes"] / (us_b_est * 1e-6) / (peaks()[0] * 1e9)
             for plb in plbs:

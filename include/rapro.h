@@ -107,9 +107,14 @@ typedef enum {
    * estimate rounded to BF16; relative filter error ~ 2^-8).  Needs the orthogonal layout,
    * an even B <= 2048 dividing n_sc and 16-byte aligned arrays; rapro_ce_lmmse_subblock and
    * w_override are not available (RAPRO_ERR_UNSUPPORTED).  The detector of such a plan
-   * falls back to FP64 for every subcarrier whose FP32 Cholesky pivots give
-   * (max L_jj / min L_jj)^2 > 1e6 (a lower bound of cond(A)) or fail: Eq. 22 solved again
-   * in FP64 by an extra kernel, which overwrites that subcarrier's outputs and info. */
+   * (rapro_detector_form, default RAPRO_DET_REFINED) forms the Gram H^H H + sigma2 I and
+   * H^H y on the tensor cores from BF16 operands (FP32 accumulation), factors it in FP32 and
+   * takes one FP32 refinement step with the residual H^H (y - H x~) - sigma2 x~ from the
+   * FP32 h (16-byte aligned h and y_data and an even n_sc; other arrays take the FP32
+   * detector).  Either detector falls back to FP64 for every subcarrier whose FP32
+   * Cholesky pivots give (max L_jj / min L_jj)^2 > 1e6 (a lower bound of cond(A)) or fail:
+   * Eq. 22 solved again in FP64 by the last CTA, which overwrites that subcarrier's outputs
+   * and info. */
   RAPRO_PREC_BF16 = 1,
   /* As RAPRO_PREC_BF16 with FP16 operands (11 significant bits, range +-65504: relative
    * filter error ~ 2^-10 for the O(1) LS estimates and weights of unit-power channels);
@@ -130,6 +135,15 @@ typedef enum {
    * small subframes (one launch) and some block sizes; rapro_plan_tune picks the faster. */
   RAPRO_RECV_FUSED = 1
 } rapro_receive_form;
+
+/* Detector of a RAPRO_PREC_BF16 / _FP16 plan (no counterpart in the paper).  The refined
+ * form follows the precision form as specified; at D data symbols per slot its FP32 residual
+ * costs 2 M K D complex multiply-adds per subcarrier, about what the FP32 Gram and matched
+ * filter cost (M K (K + 1) / 2 + M K D), so the FP32 form is the faster one at D ~ K/2. */
+typedef enum {
+  RAPRO_DET_REFINED = 0,   /* tensor-core Gram of 16-bit operands + one FP32 refinement step */
+  RAPRO_DET_FP32 = 1       /* the FP32 detector (Gram and matched filter in FP32 FMAs) */
+} rapro_detector_form;
 
 #define RAPRO_MAX_PILOT_SYM 8
 #define RAPRO_MAX_USERS 16       /* K limit of the register-tiled detector */
@@ -316,6 +330,11 @@ rapro_status rapro_plan_set_variant(rapro_plan* plan, int est_variant, int det_s
 /* Set the plan's receive form (rapro_receive_form; RAPRO_ERR_INVALID_ARG otherwise).  Not
  * while another stream uses the plan. */
 rapro_status rapro_plan_set_receive_form(rapro_plan* plan, int form);
+
+/* Set the detector form of a RAPRO_PREC_BF16 / _FP16 plan (rapro_detector_form;
+ * RAPRO_ERR_INVALID_ARG for another value, RAPRO_ERR_UNSUPPORTED for an FP32 plan).  Not
+ * while another stream uses the plan. */
+rapro_status rapro_plan_set_detector_form(rapro_plan* plan, int form);
 
 /* *fused = 1 if rapro_receive_subframe with these y_pilot and y_data pointers runs the fused
  * kernel under the plan's current form, else 0.  No device work. */

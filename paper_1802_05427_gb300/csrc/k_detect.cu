@@ -115,7 +115,8 @@ cudaError_t launch_detect(const Plan& pl, const float2* h, const float2* y, floa
                           unsigned char* labels, float* llr, int* info, cudaStream_t st) {
   // Precision form: Gram on the tensor cores, one FP32 refinement step (shape rules of the
   // tensor-core Gram; other inputs take the FP32 detector with the FP64 fallback).
-  if (half_precision(pl.p) && refine_ok(pl, h, y)) return launch_detect_refine(pl, h, y, x_eq, labels, llr, info, st);
+  if (half_precision(pl.p) && pl.det_form == RAPRO_DET_REFINED && refine_ok(pl, h, y))
+    return launch_detect_refine(pl, h, y, x_eq, labels, llr, info, st);
   DetParams P{};
   P.T = pl.T; P.K = pl.p.K; P.M = pl.p.M; P.N = pl.p.n_sc; P.D = pl.D; P.q = pl.q;
   P.sigma2 = float(pl.p.sigma2);

@@ -198,6 +198,18 @@ rapro_status rapro_plan_set_variant(rapro_plan* plan, int est_variant, int det_s
   return RAPRO_OK;
 }
 
+rapro_status rapro_plan_set_detector_form(rapro_plan* plan, int form) {
+  if (!plan) return bad("plan is NULL");
+  if (form != RAPRO_DET_REFINED && form != RAPRO_DET_FP32) return bad("form must be a rapro_detector_form");
+  Plan* pl = reinterpret_cast<Plan*>(plan);
+  if (!half_precision(pl->p)) {
+    set_error("the detector form applies to RAPRO_PREC_BF16 and RAPRO_PREC_FP16 plans");
+    return RAPRO_ERR_UNSUPPORTED;
+  }
+  pl->det_form = form;
+  return RAPRO_OK;
+}
+
 rapro_status rapro_plan_set_wait_test(rapro_plan* plan, int stall_producer, uint32_t wait_rounds) {
   if (!plan) return bad("plan is NULL");
   Plan* pl = reinterpret_cast<Plan*>(plan);

@@ -58,6 +58,7 @@ struct Plan {
   int est_ctas_per_sm = 1;
   int* d_fix = nullptr;            // precision form: FP64-fallback count, ticket, list [T n_sc]
   float2* d_gram = nullptr;        // precision form: tensor-core Gram | matched filter [T][n_sc][K][K + D]
+  int det_form = RAPRO_DET_REFINED; // detector of a 16-bit plan (rapro_detector_form)
   uint32_t wait_rounds = 0;        // diagnostics (rapro_plan_set_wait_test): detector handoff wait limit
   int stall_producer = 0;          //   and a load producer that posts nothing
   bool comb = false;               // comb pilot layout (Sec. II)

@@ -24,6 +24,7 @@ RAPRO_PDP_EXP, RAPRO_PDP_UNIFORM_L = 0, 1
 RAPRO_COMB_3W, RAPRO_COMB_SW, RAPRO_COMB_INTERP3 = 0, 1, 2
 RAPRO_PREC_FP32, RAPRO_PREC_BF16, RAPRO_PREC_FP16 = 0, 1, 2
 RAPRO_RECV_SPLIT, RAPRO_RECV_FUSED = 0, 1
+RAPRO_DET_REFINED, RAPRO_DET_FP32 = 0, 1
 RAPRO_MAX_PILOT_SYM = 8
 
 
@@ -94,6 +95,7 @@ def lib() -> ctypes.CDLL:
         "rapro_noalloc_status": ([ctypes.c_int, _P, _P], ctypes.c_int),
         "rapro_gram_tc": ([_P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
         "rapro_plan_set_wait_test": ([_P, ctypes.c_int, ctypes.c_uint32], ctypes.c_int),
+        "rapro_plan_set_detector_form": ([_P, ctypes.c_int], ctypes.c_int),
         "rapro_measure_ffma_peak": ([ctypes.c_int, _P, _P, _P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -423,6 +425,10 @@ def rapro_receive_subframe_noalloc(params: RaproParams, y_pilot, pilots, y_data,
         _ptr(y_data, (T * D, M, N), c64, "y_data"), _ptr(x_eq, (T * D, K, N), c64, "x_eq"),
         _ptr(labels, (T * D, K, N), torch.uint8, "labels"), _ptr(llr, (T * D, K, N, q), torch.float32, "llr"),
         _ptr(info, (T, N), torch.int32, "info"), _stream(stream)), "rapro_receive_subframe_noalloc")
+
+
+def rapro_plan_set_detector_form(plan: Plan, form: int) -> None:
+    _check(lib().rapro_plan_set_detector_form(plan.handle, int(form)), "rapro_plan_set_detector_form")
 
 
 def rapro_plan_set_wait_test(plan: Plan, stall_producer: bool, wait_rounds: int) -> None:

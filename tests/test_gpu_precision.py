@@ -128,3 +128,26 @@ def test_refined_detector_matches_the_oracle_refinement(dims, form):
     xh, _ = O.unbias(x1, s1, D)
     safe = O.boundary_margin(xh, q) > 1e-3
     np.testing.assert_array_equal(lab[safe], O.hard_decision(xh, q)[safe])
+
+
+def test_sixteen_bit_plans_can_take_the_fp32_detector():
+    """RAPRO_DET_FP32 on a BF16 plan: the FP32 Gram and matched filter (Eq. 22) at the FP32
+    bar against the oracle; the form is rejected for an FP32 plan and for unknown values."""
+    sh = synth.SubframeShape(M=24, K=6, n_sc=96, n_fft=128, n_data_per_slot=6, snr_db=15.0, qam_bits=4)
+    h, y = _channel_and_data(sh, 47)
+    p = params_for(sh, 8)
+    p.precision = R.RAPRO_PREC_BF16
+    plan = R.Plan(p)
+    R.rapro_plan_set_detector_form(plan, R.RAPRO_DET_FP32)
+    x, lab, llr, info = _detect(plan, h, y, sh)
+    assert plan.device_status() == 0 and (info == 0).all()
+    x_o, _ = O.mmse_detect(h.astype(np.complex128), y.astype(np.complex128), sh.sigma2, sh.n_data_per_slot)
+    assert_parity(x, x_o, (2,), 1e-5, what="FP32 detector of a BF16 plan")
+    with pytest.raises(R.RaproError) as e:
+        R.rapro_plan_set_detector_form(plan, 7)
+    assert e.value.status == R.RAPRO_ERR_INVALID_ARG
+    plan.close()
+    with R.Plan(params_for(sh, 8)) as p32:
+        with pytest.raises(R.RaproError) as e:
+            R.rapro_plan_set_detector_form(p32, R.RAPRO_DET_FP32)
+        assert e.value.status == R.RAPRO_ERR_UNSUPPORTED
