@@ -16,7 +16,7 @@
 // subcarriers 0-3 and 4-7 form two N-tiles of 4 x 2C columns (padded to a multiple of 16),
 // one accumulator each in tensor memory.  The MMA also forms the products of one
 // subcarrier's users with another's columns; only the diagonal blocks are read back, so the
-// tensor cores do about 1/4 useful work (K = 12, D = 6: 12 x 36 of every 128 x 36 rows).
+// tensor cores do about a tenth useful work (K = 12, D = 6: 12 of every 128 rows).
 //
 // One CTA per (slot, 8 subcarriers), four roles ordered by mbarriers only:
 //  * a TMA warp streams 8-antenna chunks (8 subcarriers x 8 antennas x K users of h and x D

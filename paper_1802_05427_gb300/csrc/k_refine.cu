@@ -114,18 +114,31 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
     named_bar_sync(1, RF_CONS);
 
     // ------------------------------------------------ 2. r = H^H (y - H x0) - sigma2 x0
-    constexpr int U = (DET_SC * KT * DT + RF_CONS - 1) / RF_CONS;   // (subcarrier, user, symbol) items per thread
-    float2 racc[U];
-    int hoff[U], eoff[U];
-    const int n_items = DET_SC * K * D;
+    // e = y - H x0: thread (subcarrier, antenna of the chunk, half of the symbols); its x0
+    // values stay in registers across chunks when they fit.
+    constexpr int NB1 = DT / 2;
+    constexpr bool CACHE = KT * NB1 <= 36;
+    const int e_sc = tid & (DET_SC - 1), e_m = (tid >> 4) & (DET_MCH - 1), e_n0 = (tid >> 7) * NB1;
+    float2 xc[CACHE ? KT : 1][CACHE ? NB1 : 1];
+    if constexpr (CACHE) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      racc[u] = make_float2(0.f, 0.f);
-      const int it = tid + u * RF_CONS;
-      const int sc = it % DET_SC, k = (it / DET_SC) % K, n = it / (DET_SC * K);
-      hoff[u] = it < n_items ? k * PL + sc : -1;
-      eoff[u] = n * PL + sc;
+      for (int k = 0; k < KT; ++k)
+#pragma unroll
+        for (int j = 0; j < NB1; ++j)
+          xc[k][j] = (k < K && e_n0 + j < D) ? Xs[((e_n0 + j) * KT + k) * XS + e_sc] : make_float2(0.f, 0.f);
     }
+    // r += H^H e: thread pair (subcarrier, 4 users, 3 symbols), one thread per half of the
+    // chunk's antennas; the halves meet by a shuffle at the end.
+    constexpr int KG = KT / 4, NG2 = DT / 3, COMBOS = DET_SC * KG * NG2;
+    constexpr int CPT = (COMBOS + RF_CONS / 2 - 1) / (RF_CONS / 2);
+    const int mh = tid & 1, pair = tid >> 1;
+    float2 racc[CPT][4][3];
+#pragma unroll
+    for (int u = 0; u < CPT; ++u)
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) racc[u][a2][j] = make_float2(0.f, 0.f);
     bool aborted = false;
     for (int c = 0; c < P.nchunks; ++c) {
       const int s = c % DET_STAGES;
@@ -140,28 +153,48 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
       }
       const float2* st = stage0 + size_t(s) * stage_elems;
       if (!aborted) {
-        for (int idx = tid; idx < D * PL; idx += RF_CONS) {
-          const int n = idx / PL, rem = idx - n * PL, sc = rem & (DET_SC - 1);
-          float2 e = st[yoff + idx];
-          const float2* x0 = Xs + n * KT * XS + sc;
+        const int rem = e_m * DET_SC + e_sc;
+        float2 hv[KT];
 #pragma unroll
-          for (int k = 0; k < KT; ++k) {
-            if (k < K) {
-              const float2 hv = st[k * PL + rem], xv = x0[k * XS];
-              e.x -= hv.x * xv.x - hv.y * xv.y;
-              e.y -= hv.x * xv.y + hv.y * xv.x;
+        for (int k = 0; k < KT; ++k) hv[k] = k < K ? st[k * PL + rem] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < NB1; ++j) {
+          const int n = e_n0 + j;
+          if (n < D) {
+            float2 e = st[yoff + n * PL + rem];
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+              if (k < K) {
+                const float2 xv = CACHE ? xc[CACHE ? k : 0][CACHE ? j : 0] : Xs[(n * KT + k) * XS + e_sc];
+                e.x -= hv[k].x * xv.x - hv[k].y * xv.y;
+                e.y -= hv[k].x * xv.y + hv[k].y * xv.x;
+              }
             }
+            Es[n * PL + rem] = e;
           }
-          Es[idx] = e;
         }
       }
       named_bar_sync(1, RF_CONS);
       if (!aborted) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (hoff[u] >= 0) {
+        for (int u = 0; u < CPT; ++u) {
+          const int cmb = pair + u * (RF_CONS / 2);
+          if (cmb < COMBOS) {
+            const int sc = cmb & (DET_SC - 1), kg = (cmb >> 4) % KG, ng = (cmb >> 4) / KG;
 #pragma unroll
-            for (int m = 0; m < DET_MCH; ++m) cmac_conj(racc[u], st[hoff[u] + m * DET_SC], Es[eoff[u] + m * DET_SC]);
+            for (int mm = 0; mm < DET_MCH / 2; ++mm) {
+              const int rem = (mh * (DET_MCH / 2) + mm) * DET_SC + sc;
+              float2 hv[4], ev[3];
+#pragma unroll
+              for (int a2 = 0; a2 < 4; ++a2)
+                hv[a2] = 4 * kg + a2 < K ? st[(4 * kg + a2) * PL + rem] : make_float2(0.f, 0.f);
+#pragma unroll
+              for (int j = 0; j < 3; ++j) ev[j] = 3 * ng + j < D ? Es[(3 * ng + j) * PL + rem] : make_float2(0.f, 0.f);
+#pragma unroll
+              for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) cmac_conj(racc[u][a2][j], hv[a2], ev[j]);
+            }
           }
         }
       }
@@ -170,14 +203,32 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
       named_bar_sync(1, RF_CONS);
     }
     // ------------------------------------------------ 3. x = x0 + A_low^-1 r
-    if (!aborted) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (hoff[u] >= 0) {
-          const int it = tid + u * RF_CONS;
-          const int sc = it % DET_SC, k = (it / DET_SC) % K, n = it / (DET_SC * K);
-          const float2 xv = Xs[(n * KT + k) * XS + sc];
-          Zs[(sc * KT + k) * DT + n] = make_float2(racc[u].x - P.sigma2 * xv.x, racc[u].y - P.sigma2 * xv.y);
+    for (int u = 0; u < CPT; ++u)
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          racc[u][a2][j].x += __shfl_xor_sync(0xffffffffu, racc[u][a2][j].x, 1);
+          racc[u][a2][j].y += __shfl_xor_sync(0xffffffffu, racc[u][a2][j].y, 1);
+        }
+    if (!aborted && mh == 0) {
+#pragma unroll
+      for (int u = 0; u < CPT; ++u) {
+        const int cmb = pair + u * (RF_CONS / 2);
+        if (cmb < COMBOS) {
+          const int sc = cmb & (DET_SC - 1), kg = (cmb >> 4) % KG, ng = (cmb >> 4) / KG;
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              const int k = 4 * kg + a2, n = 3 * ng + j;
+              if (k < K && n < D) {
+                const float2 xv = Xs[(n * KT + k) * XS + sc];
+                Zs[(sc * KT + k) * DT + n] =
+                    make_float2(racc[u][a2][j].x - P.sigma2 * xv.x, racc[u][a2][j].y - P.sigma2 * xv.y);
+              }
+            }
         }
       }
     }
@@ -246,6 +297,7 @@ cudaError_t refine_prepare_kt() {
 }
 
 static_assert(refine_smem_bytes<16, 12>() <= 232448, "the refine kernel's largest tile fits in shared memory");
+static_assert(RF_CONS == 256 && DET_SC == 16 && DET_MCH == 8, "the residual's thread maps assume 256 consumers, 16 x 8 tiles");
 
 }  // namespace
 
