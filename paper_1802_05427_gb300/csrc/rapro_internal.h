@@ -108,6 +108,10 @@ cudaError_t launch_adjoint(const Plan& pl, const float2* y_pilot, const float2* 
                            const float2* h, const float2* x_eq, const float2* x_ref, float2* g_h, float* scal,
                            float2* g_wm, float2* g_wt, cudaStream_t st);
 cudaError_t prepare_adjoint(int device);
+// The detector part of the adjoint (k_adj_detect.cu): G_H, the loss and dL/dsigma2 into scal.
+cudaError_t launch_adj_detect(const Plan& pl, const float2* h, const float2* y, const float2* x_eq,
+                              const float2* x_ref, float2* g_h, float* scal, cudaStream_t st);
+cudaError_t prepare_adj_detect(int device);
 
 // Kernel launchers (return the launch error, if any).
 cudaError_t launch_ls(const float2* y, const float2* pil, float2* h, int T, int K, int M,
