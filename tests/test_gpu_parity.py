@@ -605,6 +605,7 @@ def test_bf16_form_keeps_nmse_and_evm_within_a_tenth_of_a_db(form, B):
 ADJ_CASES = [
     # M, K, N, n_fft, B, D
     (6, 2, 30, 64, 7, 3), (32, 4, 120, 256, 12, 6), (17, 5, 100, 256, 9, 4), (128, 16, 1200, 2048, 12, 6),
+    (24, 3, 100, 256, 16, 3), (10, 2, 90, 256, 24, 2), (9, 2, 140, 256, 20, 2), (8, 3, 180, 256, 36, 3),
 ]
 
 
