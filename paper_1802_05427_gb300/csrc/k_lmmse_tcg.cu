@@ -53,8 +53,10 @@ __host__ __device__ constexpr int g_parts(int op) { return op == G_TF32X3 ? 2 : 
 __host__ __device__ constexpr int g_a_part(int op) { return G_ROWS * G_KC * g_elt(op); }
 constexpr int G_RAW = G_ROWS * (G_KC / 2) * 8;  // one raw chunk (bytes)
 // The tensor cores' FP32 accumulation of one sum loses accuracy linearly in its length, so
-// every G_DR chunks (K = 128 reals) the accumulator is drained into FP32 registers (rounded
-// to nearest) and the next group starts afresh in the other accumulator.
+// in the TF32 form (FP32 accuracy) every G_DR chunks (K = 128 reals) the accumulator is
+// drained into FP32 registers (rounded to nearest) and the next group starts afresh in the
+// other accumulator.  The 16-bit forms (operands rounded to 2^-9 / 2^-11) accumulate a
+// tile's whole K in one accumulator and drain it once.
 constexpr int G_DR = 4;
 
 template <int NT, int OP>
@@ -104,7 +106,8 @@ __host__ __device__ constexpr int tmem_cols(int nt) { return nt <= 32 ? 32 : nt 
 
 }  // namespace
 
-// NT: output reals per tile (a multiple of 32, at most 128).  LS: the input is y_pilot and
+// NT: output reals per tile (a multiple of 32, at most 128 for TF32 and 256 for the 16-bit
+// forms).  LS: the input is y_pilot and
 // LS is applied on load (else the input is h_ls).  OP: operand form (G_TF32X3, G_BF16,
 // G_FP16; the 16-bit forms are one pass with no lo parts).  Persistent: CTA i takes the
 // contiguous run of output tiles [n_tiles i / grid, n_tiles (i + 1) / grid), tile index =
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     lmmse_tcg_kernel(const __grid_constant__ CUtensorMap map_x, const float2* __restrict__ pil,
                      float2* __restrict__ out, const unsigned char* __restrict__ w_tiles, int R, int M, int N,
                      int B, int n_kc, int n_rt, int n_ct, int n_tiles, int w_resident, int* status) {
-  static_assert(NT % 32 == 0 && NT <= 128, "NT: 32-column read-back groups");
+  static_assert(NT % 32 == 0 && NT <= (OP == G_TF32X3 ? 128 : 256), "NT: 32-column read-back groups");
   constexpr int ELT = g_elt(OP), NP = g_parts(OP), G_A_PART = g_a_part(OP);
   constexpr uint32_t G_SBO = g_sbo(OP);
   constexpr int W_PART = NT * G_KC * ELT;          // one part of a W chunk (bytes)
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   const int t_begin = int((long long)n_tiles * blockIdx.x / gridDim.x);
   const int my_tiles = int((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) - t_begin;
   const int n_q = my_tiles * n_kc;                      // chunks of the CTA's stream
+  const int dr = OP == G_TF32X3 ? G_DR : n_kc;          // chunks per drain group
   // tile li of this CTA -> (block, first row, column tile)
   auto tile = [&](int li, int& b, int& r0, int& ct) {
     const int t = t_begin + li;
@@ -224,12 +228,12 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     if (lane == 0 && n_q > 0) {
       int issued = 0;
       bool bad = false;
-      const int gpt = (n_kc + G_DR - 1) / G_DR;         // drain groups per tile
+      const int gpt = (n_kc + dr - 1) / dr;             // drain groups per tile
       for (int q = 0; q < n_q; ++q) {
         const int li = q / n_kc, c = q - li * n_kc, ab = q & 1;
-        const int gg = li * gpt + c / G_DR;             // group of the CTA's stream
+        const int gg = li * gpt + c / dr;               // group of the CTA's stream
         // accumulator gg & 1 was last drained for group gg - 2
-        if (c % G_DR == 0 && gg >= 2 && !mbar_wait_bounded(&drained[gg & 1], uint32_t((gg - 2) >> 1) & 1u)) {
+        if (c % dr == 0 && gg >= 2 && !mbar_wait_bounded(&drained[gg & 1], uint32_t((gg - 2) >> 1) & 1u)) {
           bad = true;
           break;
         }
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         for (int ks = 0; ks < KSTEPS; ++ks) {
           const uint64_t dah = smem_desc_kmajor(ah + ks * 256, 128, G_SBO);
           const uint64_t dwh = smem_desc_kmajor(wh + ks * 256, 128, G_SBO);
-          mma_g<NT, OP>(d, dah, dwh, c % G_DR > 0 || ks > 0);
+          mma_g<NT, OP>(d, dah, dwh, c % dr > 0 || ks > 0);
           if constexpr (OP == G_TF32X3) {
             mma_g<NT, OP>(d, dah, smem_desc_kmajor(wl + ks * 256, 128, G_SBO), true);
             mma_g<NT, OP>(d, smem_desc_kmajor(al + ks * 256, 128, G_SBO), dwh, true);
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     // registers; after a tile's last group the registers (16 complex outputs of the row per
     // column group) are stored and cleared.  Waits for the MMAs of the group's last chunk,
     // then frees the accumulator.
-    const int gpt = (n_kc + G_DR - 1) / G_DR;
+    const int gpt = (n_kc + dr - 1) / dr;
     float acc_r[2][32];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -280,42 +284,69 @@ __global__ void __launch_bounds__(G_THREADS, 1)
       for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
     auto drain = [&](int gg) -> bool {
       const int li = gg / gpt, gc = gg - li * gpt;
-      const int ql = li * n_kc + min((gc + 1) * G_DR, n_kc) - 1;
+      const int ql = li * n_kc + min((gc + 1) * dr, n_kc) - 1;
       if (!mbar_wait_bounded(&done[ql & 1], uint32_t(ql >> 1) & 1u)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int rq = warp & 3;
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int g = (warp >> 2) + 2 * i;
-        if (g < NT / 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + (uint32_t(32 * rq) << 16) + uint32_t((gg & 1) * tmem_cols(NT) + 32 * g), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc_r[i][j] += __uint_as_float(v[j]);
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&drained[gg & 1]);
-      if (gc == gpt - 1) {
+      if constexpr (OP != G_TF32X3) {
+        // one group per tile: each 32-column group goes from TMEM straight to the output
         int b, r0, ct;
         tile(li, b, r0, ct);
         const int row = r0 + 32 * rq + lane;
 #pragma unroll
+        for (int i = 0; i < (NT / 32 + 1) / 2; ++i) {
+          const int g = (warp >> 2) + 2 * i;
+          if (g < NT / 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (uint32_t(32 * rq) << 16) + uint32_t((gg & 1) * tmem_cols(NT) + 32 * g), v);
+            const int j0 = (ct * NT + 32 * g) >> 1;
+            if (row < R) {
+              float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (j0 + 2 * j < B)
+                  o[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                     __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&drained[gg & 1]);
+        return true;
+      } else {
+  #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const int g = (warp >> 2) + 2 * i;
-          const int j0 = (ct * NT + 32 * g) >> 1;     // first complex output of the group
-          if (g < NT / 32 && row < R) {
-            // pairs of outputs as 16-byte stores (row * N + b * B + j0 is even; so is B)
-            float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (j0 + 2 * j < B) o[j] = make_float4(acc_r[i][4 * j], acc_r[i][4 * j + 1], acc_r[i][4 * j + 2], acc_r[i][4 * j + 3]);
+          if (g < NT / 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (uint32_t(32 * rq) << 16) + uint32_t((gg & 1) * tmem_cols(NT) + 32 * g), v);
+  #pragma unroll
+            for (int j = 0; j < 32; ++j) acc_r[i][j] += __uint_as_float(v[j]);
           }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&drained[gg & 1]);
+        if (gc == gpt - 1) {
+          int b, r0, ct;
+          tile(li, b, r0, ct);
+          const int row = r0 + 32 * rq + lane;
+  #pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const int g = (warp >> 2) + 2 * i;
+            const int j0 = (ct * NT + 32 * g) >> 1;     // first complex output of the group
+            if (g < NT / 32 && row < R) {
+              // pairs of outputs as 16-byte stores (row * N + b * B + j0 is even; so is B)
+              float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
+  #pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (j0 + 2 * j < B) o[j] = make_float4(acc_r[i][4 * j], acc_r[i][4 * j + 1], acc_r[i][4 * j + 2], acc_r[i][4 * j + 3]);
+            }
+  #pragma unroll
+            for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
+          }
+        }
+        return true;
       }
-      return true;
     };
     // Element map of a chunk (128 rows x 8 float4 of two subcarriers): warp w, lane l takes
     // rows (2w + u) * 8 + (l & 7) and float4 columns c4 = ((l >> 3) + 4h + row) & 7 (u, h in
@@ -396,8 +427,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         mbar_arrive(&aready[ab]);
         mbar_arrive(&rawfree[s]);
         // the first chunk of group gg is handed over: drain the previous group meanwhile
-        const int gg = li * gpt + c / G_DR;
-        if (c % G_DR == 0 && gg >= 1 && !drain(gg - 1)) bad = true;
+        const int gg = li * gpt + c / dr;
+        if (c % dr == 0 && gg >= 1 && !drain(gg - 1)) bad = true;
       }
     }
     if (!bad && my_tiles > 0 && !drain(my_tiles * gpt - 1)) bad = true;
@@ -411,7 +442,9 @@ __global__ void __launch_bounds__(G_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------ host
-static int tcg_nt(int B) { return 2 * B <= 96 ? 96 : 128; }
+// Output reals per tile: 96 or 128, and 256 for the 16-bit forms from B = 128 (each converted
+// A chunk then feeds twice the MMA work).
+static int tcg_nt(int B, int op) { return 2 * B <= 96 ? 96 : (op != G_TF32X3 && B >= 128 ? 256 : 128); }
 
 template <int NT, int OP>
 static size_t tcg_smem_bytes(int w_chunks) {
@@ -443,7 +476,7 @@ bool lmmse_tcg_shape_ok(const Plan& pl) {
 void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out) {
   const int op = tcg_op(pl), elt = g_elt(op), np = g_parts(op);
   const uint32_t sbo = g_sbo(op);
-  const int B = pl.B, NT = tcg_nt(B), K2 = 2 * B;
+  const int B = pl.B, NT = tcg_nt(B, op), K2 = 2 * B;
   const int n_nt = (K2 + NT - 1) / NT, n_kc = (K2 + G_KC - 1) / G_KC;
   const size_t part = size_t(NT) * G_KC * elt;
   out.assign(size_t(n_nt) * n_kc * np * part, 0);
@@ -526,12 +559,18 @@ static cudaError_t launch_tcg_nt(const Plan& pl, const float2* x, const float2* 
 }
 
 cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st) {
-  const bool n96 = tcg_nt(pl.B) == 96;
-  switch (tcg_op(pl)) {
-    case G_BF16: return n96 ? launch_tcg_nt<96, G_BF16>(pl, x, pil, out, st) : launch_tcg_nt<128, G_BF16>(pl, x, pil, out, st);
-    case G_FP16: return n96 ? launch_tcg_nt<96, G_FP16>(pl, x, pil, out, st) : launch_tcg_nt<128, G_FP16>(pl, x, pil, out, st);
+  const int op = tcg_op(pl), nt = tcg_nt(pl.B, op);
+  switch (op) {
+    case G_BF16:
+      return nt == 96    ? launch_tcg_nt<96, G_BF16>(pl, x, pil, out, st)
+             : nt == 128 ? launch_tcg_nt<128, G_BF16>(pl, x, pil, out, st)
+                         : launch_tcg_nt<256, G_BF16>(pl, x, pil, out, st);
+    case G_FP16:
+      return nt == 96    ? launch_tcg_nt<96, G_FP16>(pl, x, pil, out, st)
+             : nt == 128 ? launch_tcg_nt<128, G_FP16>(pl, x, pil, out, st)
+                         : launch_tcg_nt<256, G_FP16>(pl, x, pil, out, st);
     default:
-      return n96 ? launch_tcg_nt<96, G_TF32X3>(pl, x, pil, out, st) : launch_tcg_nt<128, G_TF32X3>(pl, x, pil, out, st);
+      return nt == 96 ? launch_tcg_nt<96, G_TF32X3>(pl, x, pil, out, st) : launch_tcg_nt<128, G_TF32X3>(pl, x, pil, out, st);
   }
 }
 
@@ -550,6 +589,8 @@ cudaError_t prepare_lmmse_tcg(int device) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_BF16>, A, S);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true, G_FP16>, A, S);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_FP16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<256, true, G_BF16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<256, true, G_FP16>, A, S);
     result[device] = e;
   });
   return result[device];

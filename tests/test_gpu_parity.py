@@ -546,7 +546,9 @@ HALF_FORMS = {"bf16": (R.RAPRO_PREC_BF16, TOL_BF16), "fp16": (R.RAPRO_PREC_FP16,
                                   (2, 1, 64, 128, 2), (128, 12, 1200, 2048, 12),
                                   # larger blocks: the tensor-core GEMM with 16-bit operands
                                   (20, 3, 72, 128, 18), (7, 2, 96, 128, 48), (16, 2, 200, 256, 100),
-                                  (33, 4, 240, 512, 80), (128, 12, 1200, 2048, 1200)])
+                                  (33, 4, 240, 512, 80), (128, 12, 1200, 2048, 1200),
+                                  # 256-column tiles: one tile (W resident), a ragged last tile
+                                  (9, 2, 256, 512, 128), (11, 3, 600, 1024, 300)])
 def test_bf16_estimator_parity(case, form):
     M, K, N, nfft, B = case
     sh = synth.SubframeShape(M=M, K=K, n_sc=N, n_fft=nfft, n_taps=24 if nfft >= 2048 else 6,
