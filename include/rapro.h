@@ -20,12 +20,14 @@
  *    reported through the info array and rapro_plan_device_status.
  *  - The plan is the only library-owned memory: the weights W_b on the device, a
  *    channel-estimate workspace used by rapro_receive_subframe when h_out is NULL,
- *    and one device status word.  rapro_plan_destroy frees all of it.
+ *    the 16-bit forms' staging buffers, and one device status word.  rapro_plan_destroy frees all of it.
  *  - No call throws across the ABI, traps on the device or asserts.  NaN/Inf inputs
  *    propagate to the outputs.  Calls that share a plan may run concurrently on
  *    different streams except rapro_receive_subframe with h_out == NULL, which writes
- *    the plan's workspace, and the detector of a RAPRO_PREC_BF16 or _FP16 plan, which keeps its
- *    FP64-fallback list in the plan: serialise those per plan.
+ *    the plan's workspace, the detector of a RAPRO_PREC_BF16 or _FP16 plan, which keeps its
+ *    FP64-fallback list in the plan, and the estimator of such a plan with 16 < B (the
+ *    tensor-core GEMM), which stages its rounded LS operand in the plan: serialise those per
+ *    plan.
  *
  * Layouts (T = n_pilot_sym slots, D = n_sym / n_pilot_sym - 1 data symbols per slot):
  *   y_pilot, h_ls, h  [T][K][M][n_sc]   pilot observation of user s at antenna m

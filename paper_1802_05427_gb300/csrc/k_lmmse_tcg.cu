@@ -23,6 +23,10 @@
 // and every G_DR chunks the consumers drain the accumulator (TMEM lane = row) into FP32
 // registers while the next group's MMAs run in the other one, storing their row's outputs
 // after a tile's last group.  Only mbarriers order the roles; every wait is bounded.
+// That kernel serves the TF32 form.  The 16-bit forms round each LS value once, in a staging
+// pass that writes the A chunks of every row tile in the canonical layout to the plan's
+// buffer (tcg_stage_kernel), and lmmse_tcg16_kernel then feeds A and W chunks to tcgen05
+// by bulk copies alone, with 256-column output tiles from B = 128 and one drain per tile.
 
 #include <algorithm>
 #include <cstring>
@@ -55,8 +59,8 @@ constexpr int G_RAW = G_ROWS * (G_KC / 2) * 8;  // one raw chunk (bytes)
 // The tensor cores' FP32 accumulation of one sum loses accuracy linearly in its length, so
 // in the TF32 form (FP32 accuracy) every G_DR chunks (K = 128 reals) the accumulator is
 // drained into FP32 registers (rounded to nearest) and the next group starts afresh in the
-// other accumulator.  The 16-bit forms (operands rounded to 2^-9 / 2^-11) accumulate a
-// tile's whole K in one accumulator and drain it once.
+// other accumulator.  The 16-bit forms (operands rounded to 2^-9 / 2^-11; lmmse_tcg16_kernel)
+// accumulate a tile's whole K in one accumulator and drain it once.
 constexpr int G_DR = 4;
 
 template <int NT, int OP>
@@ -106,8 +110,7 @@ __host__ __device__ constexpr int tmem_cols(int nt) { return nt <= 32 ? 32 : nt 
 
 }  // namespace
 
-// NT: output reals per tile (a multiple of 32, at most 128 for TF32 and 256 for the 16-bit
-// forms).  LS: the input is y_pilot and
+// NT: output reals per tile (a multiple of 32, at most 128).  LS: the input is y_pilot and
 // LS is applied on load (else the input is h_ls).  OP: operand form (G_TF32X3, G_BF16,
 // G_FP16; the 16-bit forms are one pass with no lo parts).  Persistent: CTA i takes the
 // contiguous run of output tiles [n_tiles i / grid, n_tiles (i + 1) / grid), tile index =
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     lmmse_tcg_kernel(const __grid_constant__ CUtensorMap map_x, const float2* __restrict__ pil,
                      float2* __restrict__ out, const unsigned char* __restrict__ w_tiles, int R, int M, int N,
                      int B, int n_kc, int n_rt, int n_ct, int n_tiles, int w_resident, int* status) {
-  static_assert(NT % 32 == 0 && NT <= (OP == G_TF32X3 ? 128 : 256), "NT: 32-column read-back groups");
+  static_assert(NT % 32 == 0 && NT <= 128, "NT: 32-column read-back groups");
   constexpr int ELT = g_elt(OP), NP = g_parts(OP), G_A_PART = g_a_part(OP);
   constexpr uint32_t G_SBO = g_sbo(OP);
   constexpr int W_PART = NT * G_KC * ELT;          // one part of a W chunk (bytes)
@@ -144,7 +147,6 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   const int t_begin = int((long long)n_tiles * blockIdx.x / gridDim.x);
   const int my_tiles = int((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) - t_begin;
   const int n_q = my_tiles * n_kc;                      // chunks of the CTA's stream
-  const int dr = OP == G_TF32X3 ? G_DR : n_kc;          // chunks per drain group
   // tile li of this CTA -> (block, first row, column tile)
   auto tile = [&](int li, int& b, int& r0, int& ct) {
     const int t = t_begin + li;
@@ -228,12 +230,12 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     if (lane == 0 && n_q > 0) {
       int issued = 0;
       bool bad = false;
-      const int gpt = (n_kc + dr - 1) / dr;             // drain groups per tile
+      const int gpt = (n_kc + G_DR - 1) / G_DR;         // drain groups per tile
       for (int q = 0; q < n_q; ++q) {
         const int li = q / n_kc, c = q - li * n_kc, ab = q & 1;
-        const int gg = li * gpt + c / dr;               // group of the CTA's stream
+        const int gg = li * gpt + c / G_DR;             // group of the CTA's stream
         // accumulator gg & 1 was last drained for group gg - 2
-        if (c % dr == 0 && gg >= 2 && !mbar_wait_bounded(&drained[gg & 1], uint32_t((gg - 2) >> 1) & 1u)) {
+        if (c % G_DR == 0 && gg >= 2 && !mbar_wait_bounded(&drained[gg & 1], uint32_t((gg - 2) >> 1) & 1u)) {
           bad = true;
           break;
         }
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         for (int ks = 0; ks < KSTEPS; ++ks) {
           const uint64_t dah = smem_desc_kmajor(ah + ks * 256, 128, G_SBO);
           const uint64_t dwh = smem_desc_kmajor(wh + ks * 256, 128, G_SBO);
-          mma_g<NT, OP>(d, dah, dwh, c % dr > 0 || ks > 0);
+          mma_g<NT, OP>(d, dah, dwh, c % G_DR > 0 || ks > 0);
           if constexpr (OP == G_TF32X3) {
             mma_g<NT, OP>(d, dah, smem_desc_kmajor(wl + ks * 256, 128, G_SBO), true);
             mma_g<NT, OP>(d, smem_desc_kmajor(al + ks * 256, 128, G_SBO), dwh, true);
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     // registers; after a tile's last group the registers (16 complex outputs of the row per
     // column group) are stored and cleared.  Waits for the MMAs of the group's last chunk,
     // then frees the accumulator.
-    const int gpt = (n_kc + dr - 1) / dr;
+    const int gpt = (n_kc + G_DR - 1) / G_DR;
     float acc_r[2][32];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -284,69 +286,42 @@ __global__ void __launch_bounds__(G_THREADS, 1)
       for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
     auto drain = [&](int gg) -> bool {
       const int li = gg / gpt, gc = gg - li * gpt;
-      const int ql = li * n_kc + min((gc + 1) * dr, n_kc) - 1;
+      const int ql = li * n_kc + min((gc + 1) * G_DR, n_kc) - 1;
       if (!mbar_wait_bounded(&done[ql & 1], uint32_t(ql >> 1) & 1u)) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int rq = warp & 3;
-      if constexpr (OP != G_TF32X3) {
-        // one group per tile: each 32-column group goes from TMEM straight to the output
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int g = (warp >> 2) + 2 * i;
+        if (g < NT / 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + (uint32_t(32 * rq) << 16) + uint32_t((gg & 1) * tmem_cols(NT) + 32 * g), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc_r[i][j] += __uint_as_float(v[j]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&drained[gg & 1]);
+      if (gc == gpt - 1) {
         int b, r0, ct;
         tile(li, b, r0, ct);
         const int row = r0 + 32 * rq + lane;
 #pragma unroll
-        for (int i = 0; i < (NT / 32 + 1) / 2; ++i) {
-          const int g = (warp >> 2) + 2 * i;
-          if (g < NT / 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + (uint32_t(32 * rq) << 16) + uint32_t((gg & 1) * tmem_cols(NT) + 32 * g), v);
-            const int j0 = (ct * NT + 32 * g) >> 1;
-            if (row < R) {
-              float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if (j0 + 2 * j < B)
-                  o[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                     __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
-            }
-          }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&drained[gg & 1]);
-        return true;
-      } else {
-  #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const int g = (warp >> 2) + 2 * i;
-          if (g < NT / 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + (uint32_t(32 * rq) << 16) + uint32_t((gg & 1) * tmem_cols(NT) + 32 * g), v);
-  #pragma unroll
-            for (int j = 0; j < 32; ++j) acc_r[i][j] += __uint_as_float(v[j]);
+          const int j0 = (ct * NT + 32 * g) >> 1;     // first complex output of the group
+          if (g < NT / 32 && row < R) {
+            // pairs of outputs as 16-byte stores (row * N + b * B + j0 is even; so is B)
+            float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (j0 + 2 * j < B) o[j] = make_float4(acc_r[i][4 * j], acc_r[i][4 * j + 1], acc_r[i][4 * j + 2], acc_r[i][4 * j + 3]);
           }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&drained[gg & 1]);
-        if (gc == gpt - 1) {
-          int b, r0, ct;
-          tile(li, b, r0, ct);
-          const int row = r0 + 32 * rq + lane;
-  #pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const int g = (warp >> 2) + 2 * i;
-            const int j0 = (ct * NT + 32 * g) >> 1;     // first complex output of the group
-            if (g < NT / 32 && row < R) {
-              // pairs of outputs as 16-byte stores (row * N + b * B + j0 is even; so is B)
-              float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
-  #pragma unroll
-              for (int j = 0; j < 8; ++j)
-                if (j0 + 2 * j < B) o[j] = make_float4(acc_r[i][4 * j], acc_r[i][4 * j + 1], acc_r[i][4 * j + 2], acc_r[i][4 * j + 3]);
-            }
-  #pragma unroll
-            for (int j = 0; j < 32; ++j) acc_r[i][j] = 0.f;
-          }
-        }
-        return true;
       }
+      return true;
     };
     // Element map of a chunk (128 rows x 8 float4 of two subcarriers): warp w, lane l takes
     // rows (2w + u) * 8 + (l & 7) and float4 columns c4 = ((l >> 3) + 4h + row) & 7 (u, h in
@@ -427,8 +402,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         mbar_arrive(&aready[ab]);
         mbar_arrive(&rawfree[s]);
         // the first chunk of group gg is handed over: drain the previous group meanwhile
-        const int gg = li * gpt + c / dr;
-        if (c % dr == 0 && gg >= 1 && !drain(gg - 1)) bad = true;
+        const int gg = li * gpt + c / G_DR;
+        if (c % G_DR == 0 && gg >= 1 && !drain(gg - 1)) bad = true;
       }
     }
     if (!bad && my_tiles > 0 && !drain(my_tiles * gpt - 1)) bad = true;
@@ -439,6 +414,222 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TCOLS))
                  : "memory");
+}
+
+// ---------------------------------------------------------------- 16-bit forms, staged A
+// The BF16 / FP16 forms round LS once per element: tcg_stage_kernel writes h_ls of every
+// (block, 128-row tile, K chunk) as one 16-bit A chunk in the canonical K-major layout
+// (the plan's staging buffer), so that the GEMM kernel below only copies and multiplies.
+// Elements past the last row or subcarrier are zero; those of the next block that a last K
+// chunk covers meet zero rows of W.
+template <int OP>
+__global__ void __launch_bounds__(256) tcg_stage_kernel(const float2* __restrict__ y, const float2* __restrict__ pil,
+                                                        unsigned char* __restrict__ a_tiles, int R, int M, int N,
+                                                        int B, int n_kc, int n_rt) {
+  constexpr uint32_t G_SBO = g_sbo(OP);
+  const int c = blockIdx.x, rt = blockIdx.y, b = blockIdx.z;
+  const int r0 = rt * G_ROWS, x0 = b * B + c * (G_KC / 2);
+  unsigned char* a = a_tiles + ((size_t(b) * n_rt + rt) * n_kc + c) * size_t(g_a_part(OP));
+  const int c4 = threadIdx.x & 7;                    // float4 (two subcarriers) of a 16-subcarrier row
+#pragma unroll
+  for (int k = 0; k < G_ROWS * 8 / 256; ++k) {
+    const int row = (threadIdx.x >> 3) + 32 * k, rg = r0 + row, sc = x0 + 2 * c4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rg < R && sc < N) {
+      const float4 yv = __ldg(reinterpret_cast<const float4*>(y + size_t(rg) * N + sc));
+      const float4 p = __ldg(reinterpret_cast<const float4*>(pil + size_t(rg / M) * N + sc));
+      const float i0 = __fdividef(1.0f, fmaf(p.x, p.x, p.y * p.y));
+      const float i1 = __fdividef(1.0f, fmaf(p.z, p.z, p.w * p.w));
+      v = make_float4(fmaf(yv.x, p.x, yv.y * p.y) * i0, fmaf(yv.y, p.x, -yv.x * p.y) * i0,
+                      fmaf(yv.z, p.z, yv.w * p.w) * i1, fmaf(yv.w, p.z, -yv.z * p.w) * i1);   // Eq. 9
+    }
+    // four 16-bit reals: half of a 16-byte core row (eight reals)
+    const int off = (row >> 3) * int(G_SBO) + (c4 >> 1) * 128 + (row & 7) * 16 + (c4 & 1) * 8;
+    *reinterpret_cast<uint2*>(a + off) = OP == G_FP16 ? make_uint2(pack_f16x2(v.x, v.y), pack_f16x2(v.z, v.w))
+                                                      : make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+  }
+}
+
+// GEMM of the staged A chunks with W on tcgen05, 192 threads: four drain warps (warp w reads
+// TMEM lanes 32 w .. 32 w + 31, i.e. rows), one MMA warp and one copy warp.  A ring of
+// G16_NS stages holds each chunk's A (and W unless one column tile's W stays resident),
+// brought by 1-D bulk copies; the MMA warp accumulates a tile's whole K into one of two FP32
+// accumulators and commits the tile to an mbarrier, and the drain warps store that tile
+// while the next one is multiplied into the other.  Persistent CTAs take runs of tiles as
+// in lmmse_tcg_kernel; every wait is bounded.
+constexpr int G16_NS = 8;
+constexpr int G16_THREADS = 192;
+
+template <int NT, int OP>
+__global__ void __launch_bounds__(G16_THREADS, 1)
+    lmmse_tcg16_kernel(const unsigned char* __restrict__ a_tiles, const unsigned char* __restrict__ w_tiles,
+                       float2* __restrict__ out, int R, int N, int B, int n_kc, int n_rt, int n_ct, int n_tiles,
+                       int w_resident, int* status) {
+  static_assert(OP != G_TF32X3 && NT % 32 == 0 && NT <= 256, "16-bit forms, 32-column groups");
+  constexpr int A_PART = g_a_part(OP), W_PART = NT * G_KC * g_elt(OP);
+  constexpr uint32_t G_SBO = g_sbo(OP);
+  constexpr int KSTEPS = G_KC * g_elt(OP) / 32;
+  constexpr int TCOLS = 2 * tmem_cols(NT);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* pfull = reinterpret_cast<uint64_t*>(smem);   // [G16_NS] stage landed
+  uint64_t* pdone = pfull + G16_NS;                      // [G16_NS] MMAs of the stage's chunk done
+  uint64_t* tdone = pdone + G16_NS;                      // [2] a tile's MMAs done (per accumulator)
+  uint64_t* drained = tdone + 2;                         // [2] accumulator read back
+  uint64_t* wres = drained + 2;                          // resident W landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wres + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int stage_bytes = A_PART + (w_resident ? 0 : W_PART);
+  unsigned char* ring = smem + 1024;                     // [G16_NS][A | W]
+  unsigned char* sWres = ring + G16_NS * stage_bytes;    // resident W: [n_kc][W_PART]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int t_begin = int((long long)n_tiles * blockIdx.x / gridDim.x);
+  const int my_tiles = int((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) - t_begin;
+  const int n_q = my_tiles * n_kc;
+  auto tile = [&](int li, int& b, int& rt, int& ct) {
+    const int t = t_begin + li;
+    ct = t % n_ct;
+    const int rest = t / n_ct;
+    rt = rest % n_rt;
+    b = rest / n_rt;
+  };
+  if (tid == 0) {
+    for (int s = 0; s < G16_NS; ++s) {
+      mbar_init(&pfull[s], 1);
+      mbar_init(&pdone[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tdone[i], 1);
+      mbar_init(&drained[i], 128);
+    }
+    mbar_init(wres, 1);
+    *s_abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(uint32_t(TCOLS))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  auto give_up = [&]() {
+    *s_abort = 1;
+    atomicExch(status, int(RAPRO_ERR_TIMEOUT));
+  };
+  if (warp == 5) {
+    // ------------------------------------------------ copy warp
+    if (lane == 0 && n_q > 0) {
+      int issued = 0;
+      bool bad = false;
+      if (w_resident) {                         // one column tile: all of its W chunks, once
+        mbar_arrive_expect_tx(wres, uint32_t(n_kc) * W_PART);
+        bulk_load(sWres, w_tiles, uint32_t(n_kc) * W_PART, wres);
+      }
+      for (int q = 0; q < n_q && !bad; ++q) {
+        const int li = q / n_kc, c = q - li * n_kc, s = q % G16_NS;
+        int b, rt, ct;
+        tile(li, b, rt, ct);
+        // stage s was last read by the MMAs of chunk q - G16_NS
+        if (q >= G16_NS && !mbar_wait_bounded(&pdone[s], uint32_t(q / G16_NS - 1) & 1u)) {
+          bad = true;
+          break;
+        }
+        unsigned char* st = ring + s * stage_bytes;
+        mbar_arrive_expect_tx(&pfull[s], uint32_t(stage_bytes));
+        bulk_load(st, a_tiles + ((size_t(b) * n_rt + rt) * n_kc + c) * A_PART, A_PART, &pfull[s]);
+        if (!w_resident) bulk_load(st + A_PART, w_tiles + (size_t(ct) * n_kc + c) * W_PART, W_PART, &pfull[s]);
+        ++issued;
+        if (*s_abort) bad = true;
+      }
+      // Let the copies in flight land before the CTA moves on (all consumed on the normal path).
+      for (int s = 0; s < G16_NS && s < issued; ++s)
+        (void)mbar_wait_bounded(&pfull[s], uint32_t((issued - 1 - s) / G16_NS) & 1u);
+      if (w_resident) (void)mbar_wait_bounded(wres, 0u);
+      if (bad) give_up();
+    }
+  } else if (warp == 4) {
+    // ------------------------------------------------ MMA warp: one thread issues
+    if (lane == 0 && n_q > 0) {
+      int issued = 0;
+      bool bad = false;
+      if (w_resident && !mbar_wait_bounded(wres, 0u)) bad = true;
+      for (int q = 0; q < n_q && !bad; ++q) {
+        const int li = q / n_kc, c = q - li * n_kc, s = q % G16_NS;
+        // accumulator li & 1 was last drained for tile li - 2
+        if (c == 0 && li >= 2 && !mbar_wait_bounded(&drained[li & 1], uint32_t((li - 2) >> 1) & 1u)) {
+          bad = true;
+          break;
+        }
+        if (!mbar_wait_bounded(&pfull[s], uint32_t(q / G16_NS) & 1u) || *s_abort) {
+          bad = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned char* a = ring + s * stage_bytes;
+        const unsigned char* w = w_resident ? sWres + size_t(c) * W_PART : a + A_PART;
+        const uint32_t d = tmem + uint32_t((li & 1) * tmem_cols(NT));
+#pragma unroll
+        for (int ks = 0; ks < KSTEPS; ++ks)
+          mma_g<NT, OP>(d, smem_desc_kmajor(a + ks * 256, 128, G_SBO), smem_desc_kmajor(w + ks * 256, 128, G_SBO),
+                        c > 0 || ks > 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&pdone[s]))
+                     : "memory");
+        if (c == n_kc - 1)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&tdone[li & 1]))
+                       : "memory");
+        ++issued;
+      }
+      // The tensor cores finish in order: the last chunk done means TMEM may be freed.
+      if (issued > 0)
+        (void)mbar_wait_bounded(&pdone[(issued - 1) % G16_NS], uint32_t((issued - 1) / G16_NS) & 1u);
+      if (bad) give_up();
+    }
+  } else {
+    // ------------------------------------------------ drain warps: TMEM -> output
+    for (int li = 0; li < my_tiles; ++li) {
+      if (*s_abort || !mbar_wait_bounded(&tdone[li & 1], uint32_t(li >> 1) & 1u)) {
+        give_up();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int b, rt, ct;
+      tile(li, b, rt, ct);
+      const int row = rt * G_ROWS + 32 * warp + lane;
+#pragma unroll 1
+      for (int g = 0; g < NT / 32; ++g) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t((li & 1) * tmem_cols(NT) + 32 * g), v);
+        const int j0 = (ct * NT + 32 * g) >> 1;       // first complex output of the group
+        if (row < R) {
+          // pairs of outputs as 16-byte stores (row * N + b * B + j0 is even; so is B)
+          float4* o = reinterpret_cast<float4*>(out + size_t(row) * N + size_t(b) * B + j0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j0 + 2 * j < B)
+              o[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                 __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&drained[li & 1]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TCOLS))
+                 : "memory");
+}
+
+template <int NT, int OP>
+constexpr size_t tcg16_smem_bytes(int n_kc, bool w_resident) {
+  return 1024 + size_t(G16_NS) * (g_a_part(OP) + (w_resident ? 0 : NT * G_KC * g_elt(OP))) +
+         (w_resident ? size_t(n_kc) * NT * G_KC * g_elt(OP) : 0);
 }
 
 // ------------------------------------------------------------------------------ host
@@ -520,7 +711,40 @@ static PFN_cuTensorMapEncodeTiled_v12000 tcg_encode() {
 
 bool lmmse_tcg_ok(const Plan& pl, const float2* x, const float2* out) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(out);
-  return pl.d_w_tcg != nullptr && (a & 15) == 0 && lmmse_tcg_shape_ok(pl) && tcg_encode() != nullptr;
+  return pl.d_w_tcg != nullptr && (a & 15) == 0 && lmmse_tcg_shape_ok(pl) && tcg_encode() != nullptr &&
+         (tcg_op(pl) == G_TF32X3 || pl.d_a_tcg != nullptr);
+}
+
+// The 16-bit forms' staged A operand: [blocks][row tiles][K chunks] canonical chunks (0 for
+// the TF32 form and other shapes).
+size_t lmmse_tcg_stage_bytes(const Plan& pl) {
+  const int op = tcg_op(pl);
+  if (op == G_TF32X3 || !lmmse_tcg_shape_ok(pl)) return 0;
+  const long long R = (long long)pl.T * pl.p.K * pl.p.M;
+  const long long n_rt = (R + G_ROWS - 1) / G_ROWS, n_kc = (2 * pl.B + G_KC - 1) / G_KC;
+  return size_t(pl.p.n_sc / pl.B) * size_t(n_rt) * size_t(n_kc) * size_t(g_a_part(op));
+}
+
+template <int NT, int OP>
+static cudaError_t launch_tcg16(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
+  if (!pil || !pl.d_a_tcg) return cudaErrorNotSupported;   // the 16-bit forms take the LS-fused input only
+  const int B = pl.B, N = pl.p.n_sc, M = pl.p.M, R = pl.T * pl.p.K * pl.p.M;
+  const int n_nt = (2 * B + NT - 1) / NT, n_kc = (2 * B + G_KC - 1) / G_KC, n_rt = (R + G_ROWS - 1) / G_ROWS;
+  const int nb = N / B;
+  if (n_rt > 65535) return cudaErrorInvalidValue;
+  const long long tiles = (long long)n_rt * n_nt * nb;
+  if (tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+  unsigned char* a = static_cast<unsigned char*>(pl.d_a_tcg);
+  tcg_stage_kernel<OP><<<dim3(n_kc, n_rt, nb), 256, 0, st>>>(y, pil, a, R, M, N, B, n_kc, n_rt);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = int(tiles), grid = std::min(n_tiles, sms);   // one CTA per SM (shared memory, TMEM)
+  const int w_resident = n_nt == 1 && tcg16_smem_bytes<NT, OP>(n_kc, true) <= kTcgSmemMax ? 1 : 0;
+  lmmse_tcg16_kernel<NT, OP><<<grid, G16_THREADS, tcg16_smem_bytes<NT, OP>(n_kc, w_resident != 0), st>>>(
+      a, static_cast<const unsigned char*>(pl.d_w_tcg), out, R, N, B, n_kc, n_rt, n_nt, n_tiles, w_resident,
+      pl.d_status);
+  return cudaGetLastError();
 }
 
 template <int NT, int OP>
@@ -562,13 +786,13 @@ cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil,
   const int op = tcg_op(pl), nt = tcg_nt(pl.B, op);
   switch (op) {
     case G_BF16:
-      return nt == 96    ? launch_tcg_nt<96, G_BF16>(pl, x, pil, out, st)
-             : nt == 128 ? launch_tcg_nt<128, G_BF16>(pl, x, pil, out, st)
-                         : launch_tcg_nt<256, G_BF16>(pl, x, pil, out, st);
+      return nt == 96    ? launch_tcg16<96, G_BF16>(pl, x, pil, out, st)
+             : nt == 128 ? launch_tcg16<128, G_BF16>(pl, x, pil, out, st)
+                         : launch_tcg16<256, G_BF16>(pl, x, pil, out, st);
     case G_FP16:
-      return nt == 96    ? launch_tcg_nt<96, G_FP16>(pl, x, pil, out, st)
-             : nt == 128 ? launch_tcg_nt<128, G_FP16>(pl, x, pil, out, st)
-                         : launch_tcg_nt<256, G_FP16>(pl, x, pil, out, st);
+      return nt == 96    ? launch_tcg16<96, G_FP16>(pl, x, pil, out, st)
+             : nt == 128 ? launch_tcg16<128, G_FP16>(pl, x, pil, out, st)
+                         : launch_tcg16<256, G_FP16>(pl, x, pil, out, st);
     default:
       return nt == 96 ? launch_tcg_nt<96, G_TF32X3>(pl, x, pil, out, st) : launch_tcg_nt<128, G_TF32X3>(pl, x, pil, out, st);
   }
@@ -585,12 +809,12 @@ cudaError_t prepare_lmmse_tcg(int device) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, false, G_TF32X3>, A, S);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_TF32X3>, A, S);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, false, G_TF32X3>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true, G_BF16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_BF16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, true, G_FP16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_FP16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<256, true, G_BF16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<256, true, G_FP16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<96, G_BF16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<128, G_BF16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<256, G_BF16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<96, G_FP16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<128, G_FP16>, A, S);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<256, G_FP16>, A, S);
     result[device] = e;
   });
   return result[device];

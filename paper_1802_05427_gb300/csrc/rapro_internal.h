@@ -50,6 +50,7 @@ struct Plan {
   int* d_status = nullptr;         // device status word
   void* d_w_tc = nullptr;          // tensor-core filter operand (canonical layout), or null
   void* d_w_tcg = nullptr;         // large-B tensor-core GEMM operand (tiles of Wr chunks), or null
+  void* d_a_tcg = nullptr;         // 16-bit GEMM forms: staged LS operand (canonical A chunks), or null
   int est_variant = -1;            // estimator kernel (EST_*), -1 = built-in choice; set by rapro_plan_tune
   int recv_form = RAPRO_RECV_SPLIT; // rapro_receive_form of rapro_receive_subframe
   // Tensor-core estimator CTAs per SM (0: as many as fit).  One leaves each SM room for a
@@ -148,6 +149,7 @@ bool lmmse_tcg_shape_ok(const Plan& pl);
 void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out);
 bool lmmse_tcg_ok(const Plan& pl, const float2* x, const float2* out);
 cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil, float2* out, cudaStream_t st);
+size_t lmmse_tcg_stage_bytes(const Plan& pl);   // the 16-bit forms' staged operand (0: none)
 cudaError_t prepare_lmmse_tcg(int device);
 
 // Gram and matched filter on tcgen05 with 16-bit operands (precision form): G[t][k][s][c] =

@@ -461,6 +461,7 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
   auto fail = [&](cudaError_t err, const char* what) {
     cudaFree(pl->d_w_main); cudaFree(pl->d_w_tail); cudaFree(pl->d_h_work); cudaFree(pl->d_status);
     cudaFree(pl->d_w_tc); cudaFree(pl->d_w_tcg); cudaFree(pl->d_w_comb); cudaFree(pl->d_fix); cudaFree(pl->d_gram);
+    cudaFree(pl->d_a_tcg);
     delete pl;
     return cuda_fail(err, what);
   };
@@ -503,6 +504,9 @@ rapro_status rapro_plan_create(const rapro_params* p, rapro_plan** out) {
     if ((e = cudaMalloc(&pl->d_w_tcg, wtg.size())) != cudaSuccess) return fail(e, "cudaMalloc W (tensor-core GEMM)");
     if ((e = cudaMemcpy(pl->d_w_tcg, wtg.data(), wtg.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
       return fail(e, "cudaMemcpy W (tensor-core GEMM)");
+    const size_t a_bytes = lmmse_tcg_stage_bytes(*pl);
+    if (a_bytes && (e = cudaMalloc(&pl->d_a_tcg, a_bytes)) != cudaSuccess)
+      return fail(e, "cudaMalloc staged operand (tensor-core GEMM)");
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "plan upload");
   *out = reinterpret_cast<rapro_plan*>(pl);
@@ -522,6 +526,7 @@ rapro_status rapro_plan_destroy(rapro_plan* plan) {
   cudaFree(pl->d_w_comb);
   cudaFree(pl->d_fix);
   cudaFree(pl->d_gram);
+  cudaFree(pl->d_a_tcg);
   delete pl;
   return e == cudaSuccess ? RAPRO_OK : cuda_fail(e, "rapro_plan_destroy");
 }
