@@ -421,19 +421,26 @@ __global__ void __launch_bounds__(G_THREADS, 1)
 // (block, 128-row tile, K chunk) as one 16-bit A chunk in the canonical K-major layout
 // (the plan's staging buffer), so that the GEMM kernel below only copies and multiplies.
 // Elements past the last row or subcarrier are zero; those of the next block that a last K
-// chunk covers meet zero rows of W.
+// chunk covers meet zero rows of W.  Chunks of the 16-bit forms are G16_KC = 64 reals (32
+// subcarriers) wide: half as many commits and barrier round trips per MMA as 32.
+constexpr int G16_KC = 64;                      // input reals per K chunk (32 subcarriers)
+constexpr int G16_NS = 4;
+constexpr int G16_THREADS = 192;
+constexpr uint32_t G16_SBO = uint32_t(G16_KC * 2 / 16) * 128;   // 8-row group stride (bytes)
+constexpr int G16_A_PART = G_ROWS * G16_KC * 2;                 // one A chunk (bytes)
+
 template <int OP>
 __global__ void __launch_bounds__(256) tcg_stage_kernel(const float2* __restrict__ y, const float2* __restrict__ pil,
                                                         unsigned char* __restrict__ a_tiles, int R, int M, int N,
                                                         int B, int n_kc, int n_rt) {
-  constexpr uint32_t G_SBO = g_sbo(OP);
+  constexpr int F4 = G16_KC / 4;                     // float4 (two subcarriers) per chunk row
   const int c = blockIdx.x, rt = blockIdx.y, b = blockIdx.z;
-  const int r0 = rt * G_ROWS, x0 = b * B + c * (G_KC / 2);
-  unsigned char* a = a_tiles + ((size_t(b) * n_rt + rt) * n_kc + c) * size_t(g_a_part(OP));
-  const int c4 = threadIdx.x & 7;                    // float4 (two subcarriers) of a 16-subcarrier row
+  const int r0 = rt * G_ROWS, x0 = b * B + c * (G16_KC / 2);
+  unsigned char* a = a_tiles + ((size_t(b) * n_rt + rt) * n_kc + c) * size_t(G16_A_PART);
+  const int c4 = threadIdx.x % F4;
 #pragma unroll
-  for (int k = 0; k < G_ROWS * 8 / 256; ++k) {
-    const int row = (threadIdx.x >> 3) + 32 * k, rg = r0 + row, sc = x0 + 2 * c4;
+  for (int k = 0; k < G_ROWS * F4 / 256; ++k) {
+    const int row = int(threadIdx.x) / F4 + (256 / F4) * k, rg = r0 + row, sc = x0 + 2 * c4;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (rg < R && sc < N) {
       const float4 yv = __ldg(reinterpret_cast<const float4*>(y + size_t(rg) * N + sc));
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(256) tcg_stage_kernel(const float2* __restrict
                       fmaf(yv.z, p.z, yv.w * p.w) * i1, fmaf(yv.w, p.z, -yv.z * p.w) * i1);   // Eq. 9
     }
     // four 16-bit reals: half of a 16-byte core row (eight reals)
-    const int off = (row >> 3) * int(G_SBO) + (c4 >> 1) * 128 + (row & 7) * 16 + (c4 & 1) * 8;
+    const int off = (row >> 3) * int(G16_SBO) + (c4 >> 1) * 128 + (row & 7) * 16 + (c4 & 1) * 8;
     *reinterpret_cast<uint2*>(a + off) = OP == G_FP16 ? make_uint2(pack_f16x2(v.x, v.y), pack_f16x2(v.z, v.w))
                                                       : make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
   }
@@ -457,18 +464,30 @@ __global__ void __launch_bounds__(256) tcg_stage_kernel(const float2* __restrict
 // accumulators and commits the tile to an mbarrier, and the drain warps store that tile
 // while the next one is multiplied into the other.  Persistent CTAs take runs of tiles as
 // in lmmse_tcg_kernel; every wait is bounded.
-constexpr int G16_NS = 8;
-constexpr int G16_THREADS = 192;
+// PAIR (streamed W): clusters of two CTAs take the two row tiles of a pair with the same
+// column tile; each CTA brings half of every W chunk and multicasts it into both CTAs'
+// stages, so W crosses from L2 once per pair.  A stage is refilled only when the MMAs of
+// both CTAs are done with it (each commit arrives on both CTAs' barriers).  Both CTAs pass a
+// cluster barrier after setting up their barriers and before leaving.
 
-template <int NT, int OP>
+__device__ __forceinline__ void bulk_load_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar)), "h"(cta_mask)
+      : "memory");
+}
+
+template <int NT, int OP, bool PAIR>
 __global__ void __launch_bounds__(G16_THREADS, 1)
     lmmse_tcg16_kernel(const unsigned char* __restrict__ a_tiles, const unsigned char* __restrict__ w_tiles,
-                       float2* __restrict__ out, int R, int N, int B, int n_kc, int n_rt, int n_ct, int n_tiles,
-                       int w_resident, int* status) {
+                       float2* __restrict__ out, int R, int N, int B, int n_kc, int n_rt, int n_rt_a, int n_ct,
+                       int n_tiles, int w_resident, int* status) {
   static_assert(OP != G_TF32X3 && NT % 32 == 0 && NT <= 256, "16-bit forms, 32-column groups");
-  constexpr int A_PART = g_a_part(OP), W_PART = NT * G_KC * g_elt(OP);
-  constexpr uint32_t G_SBO = g_sbo(OP);
-  constexpr int KSTEPS = G_KC * g_elt(OP) / 32;
+  constexpr int A_PART = G16_A_PART, W_PART = NT * G16_KC * 2;
+  constexpr uint32_t G_SBO = G16_SBO;
+  constexpr int KSTEPS = G16_KC * 2 / 32;               // MMAs per chunk (K = 16 each)
   constexpr int TCOLS = 2 * tmem_cols(NT);
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* pfull = reinterpret_cast<uint64_t*>(smem);   // [G16_NS] stage landed
@@ -482,8 +501,13 @@ __global__ void __launch_bounds__(G16_THREADS, 1)
   unsigned char* ring = smem + 1024;                     // [G16_NS][A | W]
   unsigned char* sWres = ring + G16_NS * stage_bytes;    // resident W: [n_kc][W_PART]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int t_begin = int((long long)n_tiles * blockIdx.x / gridDim.x);
-  const int my_tiles = int((long long)n_tiles * (blockIdx.x + 1) / gridDim.x) - t_begin;
+  // PAIR: a unit of work is a pair of row tiles (n_rt counts pairs); this CTA takes row tile
+  // 2 rt + rank of each.  The staged A holds n_rt_a row tiles.
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const int unit = PAIR ? int(blockIdx.x >> 1) : int(blockIdx.x);
+  const int n_units = PAIR ? int(gridDim.x >> 1) : int(gridDim.x);
+  const int t_begin = int((long long)n_tiles * unit / n_units);
+  const int my_tiles = int((long long)n_tiles * (unit + 1) / n_units) - t_begin;
   const int n_q = my_tiles * n_kc;
   auto tile = [&](int li, int& b, int& rt, int& ct) {
     const int t = t_begin + li;
@@ -491,11 +515,12 @@ __global__ void __launch_bounds__(G16_THREADS, 1)
     const int rest = t / n_ct;
     rt = rest % n_rt;
     b = rest / n_rt;
+    if (PAIR) rt = 2 * rt + int(rank);
   };
   if (tid == 0) {
     for (int s = 0; s < G16_NS; ++s) {
       mbar_init(&pfull[s], 1);
-      mbar_init(&pdone[s], 1);
+      mbar_init(&pdone[s], PAIR ? 2 : 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tdone[i], 1);
@@ -513,6 +538,7 @@ __global__ void __launch_bounds__(G16_THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (PAIR) cluster_sync_all();                          // the peer's barriers are set up
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   auto give_up = [&]() {
@@ -539,8 +565,12 @@ __global__ void __launch_bounds__(G16_THREADS, 1)
         }
         unsigned char* st = ring + s * stage_bytes;
         mbar_arrive_expect_tx(&pfull[s], uint32_t(stage_bytes));
-        bulk_load(st, a_tiles + ((size_t(b) * n_rt + rt) * n_kc + c) * A_PART, A_PART, &pfull[s]);
-        if (!w_resident) bulk_load(st + A_PART, w_tiles + (size_t(ct) * n_kc + c) * W_PART, W_PART, &pfull[s]);
+        bulk_load(st, a_tiles + ((size_t(b) * n_rt_a + rt) * n_kc + c) * A_PART, A_PART, &pfull[s]);
+        const unsigned char* wsrc = w_tiles + (size_t(ct) * n_kc + c) * W_PART;
+        if (PAIR)          // this CTA's half of the chunk's W rows, into both CTAs' stage s
+          bulk_load_mc(st + A_PART + rank * (W_PART / 2), wsrc + rank * (W_PART / 2), W_PART / 2, &pfull[s], 0x3);
+        else if (!w_resident)
+          bulk_load(st + A_PART, wsrc, W_PART, &pfull[s]);
         ++issued;
         if (*s_abort) bad = true;
       }
@@ -575,9 +605,16 @@ __global__ void __launch_bounds__(G16_THREADS, 1)
         for (int ks = 0; ks < KSTEPS; ++ks)
           mma_g<NT, OP>(d, smem_desc_kmajor(a + ks * 256, 128, G_SBO), smem_desc_kmajor(w + ks * 256, 128, G_SBO),
                         c > 0 || ks > 0);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&pdone[s]))
-                     : "memory");
+        if (PAIR)          // stage s is free once both CTAs' MMAs are done with it
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                  smem_u32(&pdone[s])),
+              "h"(uint16_t(0x3))
+              : "memory");
+        else
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&pdone[s]))
+                       : "memory");
         if (c == n_kc - 1)
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&tdone[li & 1]))
@@ -621,6 +658,7 @@ __global__ void __launch_bounds__(G16_THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (PAIR) cluster_sync_all();                          // no copy or arrival still bound for this CTA
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TCOLS))
                  : "memory");
@@ -628,8 +666,8 @@ __global__ void __launch_bounds__(G16_THREADS, 1)
 
 template <int NT, int OP>
 constexpr size_t tcg16_smem_bytes(int n_kc, bool w_resident) {
-  return 1024 + size_t(G16_NS) * (g_a_part(OP) + (w_resident ? 0 : NT * G_KC * g_elt(OP))) +
-         (w_resident ? size_t(n_kc) * NT * G_KC * g_elt(OP) : 0);
+  return 1024 + size_t(G16_NS) * (G16_A_PART + (w_resident ? 0 : NT * G16_KC * 2)) +
+         (w_resident ? size_t(n_kc) * NT * G16_KC * 2 : 0);
 }
 
 // ------------------------------------------------------------------------------ host
@@ -666,17 +704,18 @@ bool lmmse_tcg_shape_ok(const Plan& pl) {
 // after the other.
 void build_lmmse_tcg_weights(const Plan& pl, std::vector<unsigned char>& out) {
   const int op = tcg_op(pl), elt = g_elt(op), np = g_parts(op);
-  const uint32_t sbo = g_sbo(op);
+  const int KC = op == G_TF32X3 ? G_KC : G16_KC;   // K chunk of the kernel that reads the tiles
+  const uint32_t sbo = uint32_t(KC * elt / 16) * 128;
   const int B = pl.B, NT = tcg_nt(B, op), K2 = 2 * B;
-  const int n_nt = (K2 + NT - 1) / NT, n_kc = (K2 + G_KC - 1) / G_KC;
-  const size_t part = size_t(NT) * G_KC * elt;
+  const int n_nt = (K2 + NT - 1) / NT, n_kc = (K2 + KC - 1) / KC;
+  const size_t part = size_t(NT) * KC * elt;
   out.assign(size_t(n_nt) * n_kc * np * part, 0);
   for (int t = 0; t < n_nt; ++t)
     for (int c = 0; c < n_kc; ++c) {
       unsigned char* base = out.data() + (size_t(t) * n_kc + c) * np * part;
       for (int nn = 0; nn < NT; ++nn)
-        for (int kk = 0; kk < G_KC; ++kk) {
-          const int n = t * NT + nn, k = c * G_KC + kk;
+        for (int kk = 0; kk < KC; ++kk) {
+          const int n = t * NT + nn, k = c * KC + kk;
           if (n >= K2 || k >= K2) continue;
           const float2 w = pl.w_main[size_t(n >> 1) * B + (k >> 1)];
           const float vals[2][2] = {{w.x, -w.y}, {w.y, w.x}};   // [out re/im][in re/im]
@@ -721,30 +760,54 @@ size_t lmmse_tcg_stage_bytes(const Plan& pl) {
   const int op = tcg_op(pl);
   if (op == G_TF32X3 || !lmmse_tcg_shape_ok(pl)) return 0;
   const long long R = (long long)pl.T * pl.p.K * pl.p.M;
-  const long long n_rt = (R + G_ROWS - 1) / G_ROWS, n_kc = (2 * pl.B + G_KC - 1) / G_KC;
-  return size_t(pl.p.n_sc / pl.B) * size_t(n_rt) * size_t(n_kc) * size_t(g_a_part(op));
+  const long long n_rt_a = 2 * ((R + 2 * G_ROWS - 1) / (2 * G_ROWS)), n_kc = (2 * pl.B + G16_KC - 1) / G16_KC;
+  return size_t(pl.p.n_sc / pl.B) * size_t(n_rt_a) * size_t(n_kc) * size_t(G16_A_PART);
 }
 
 template <int NT, int OP>
 static cudaError_t launch_tcg16(const Plan& pl, const float2* y, const float2* pil, float2* out, cudaStream_t st) {
   if (!pil || !pl.d_a_tcg) return cudaErrorNotSupported;   // the 16-bit forms take the LS-fused input only
   const int B = pl.B, N = pl.p.n_sc, M = pl.p.M, R = pl.T * pl.p.K * pl.p.M;
-  const int n_nt = (2 * B + NT - 1) / NT, n_kc = (2 * B + G_KC - 1) / G_KC, n_rt = (R + G_ROWS - 1) / G_ROWS;
-  const int nb = N / B;
-  if (n_rt > 65535) return cudaErrorInvalidValue;
-  const long long tiles = (long long)n_rt * n_nt * nb;
-  if (tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+  const int n_nt = (2 * B + NT - 1) / NT, n_kc = (2 * B + G16_KC - 1) / G16_KC, n_rt = (R + G_ROWS - 1) / G_ROWS;
+  const int n_rt_a = 2 * ((n_rt + 1) / 2), nb = N / B;   // staged row tiles: an even count
+  if (n_rt_a > 65535) return cudaErrorInvalidValue;
   unsigned char* a = static_cast<unsigned char*>(pl.d_a_tcg);
-  tcg_stage_kernel<OP><<<dim3(n_kc, n_rt, nb), 256, 0, st>>>(y, pil, a, R, M, N, B, n_kc, n_rt);
+  const unsigned char* w = static_cast<const unsigned char*>(pl.d_w_tcg);
+  tcg_stage_kernel<OP><<<dim3(n_kc, n_rt_a, nb), 256, 0, st>>>(y, pil, a, R, M, N, B, n_kc, n_rt_a);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int n_tiles = int(tiles), grid = std::min(n_tiles, sms);   // one CTA per SM (shared memory, TMEM)
-  const int w_resident = n_nt == 1 && tcg16_smem_bytes<NT, OP>(n_kc, true) <= kTcgSmemMax ? 1 : 0;
-  lmmse_tcg16_kernel<NT, OP><<<grid, G16_THREADS, tcg16_smem_bytes<NT, OP>(n_kc, w_resident != 0), st>>>(
-      a, static_cast<const unsigned char*>(pl.d_w_tcg), out, R, N, B, n_kc, n_rt, n_nt, n_tiles, w_resident,
-      pl.d_status);
-  return cudaGetLastError();
+  const bool w_resident = n_nt == 1 && tcg16_smem_bytes<NT, OP>(n_kc, true) <= kTcgSmemMax;
+  if (w_resident) {                                     // one column tile: no W to share
+    const long long tiles = (long long)n_rt * nb;
+    if (tiles >= (1ll << 31)) return cudaErrorInvalidValue;
+    const int n_tiles = int(tiles), grid = std::min(n_tiles, sms);   // one CTA per SM (shared memory, TMEM)
+    lmmse_tcg16_kernel<NT, OP, false><<<grid, G16_THREADS, tcg16_smem_bytes<NT, OP>(n_kc, true), st>>>(
+        a, w, out, R, N, B, n_kc, n_rt, n_rt_a, n_nt, n_tiles, 1, pl.d_status);
+    return cudaGetLastError();
+  }
+  // CTA pairs over pairs of row tiles
+  const long long tiles = (long long)(n_rt_a / 2) * n_nt * nb;
+  if (tiles >= (1ll << 30)) return cudaErrorInvalidValue;
+  const int n_tiles = int(tiles);
+  cudaLaunchConfig_t cfg{};
+  cfg.blockDim = dim3(G16_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = tcg16_smem_bytes<NT, OP>(n_kc, false);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // as many pairs as can be resident at once (pairs sit on two SMs of one GPC)
+  cfg.gridDim = dim3(2 * std::max(1, std::min(n_tiles, sms / 2)), 1, 1);
+  int fit = 0;
+  if (cudaOccupancyMaxActiveClusters(&fit, lmmse_tcg16_kernel<NT, OP, true>, &cfg) != cudaSuccess) fit = 0;
+  cfg.gridDim = dim3(2 * std::max(1, std::min({n_tiles, sms / 2, fit > 0 ? fit : sms / 2})), 1, 1);
+  return cudaLaunchKernelEx(&cfg, lmmse_tcg16_kernel<NT, OP, true>, static_cast<const unsigned char*>(a), w, out, R,
+                            N, B, n_kc, n_rt_a / 2, n_rt_a, n_nt, n_tiles, 0, pl.d_status);
 }
 
 template <int NT, int OP>
@@ -798,6 +861,18 @@ cudaError_t launch_lmmse_tcg(const Plan& pl, const float2* x, const float2* pil,
   }
 }
 
+template <int OP>
+static cudaError_t set_tcg16_smem(int bytes) {
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(lmmse_tcg16_kernel<96, OP, false>, A, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<128, OP, false>, A, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<256, OP, false>, A, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<96, OP, true>, A, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<128, OP, true>, A, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<256, OP, true>, A, bytes);
+  return e;
+}
+
 cudaError_t prepare_lmmse_tcg(int device) {
   static std::once_flag flags[64];
   static cudaError_t result[64];
@@ -809,12 +884,8 @@ cudaError_t prepare_lmmse_tcg(int device) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<96, false, G_TF32X3>, A, S);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, true, G_TF32X3>, A, S);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg_kernel<128, false, G_TF32X3>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<96, G_BF16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<128, G_BF16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<256, G_BF16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<96, G_FP16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<128, G_FP16>, A, S);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(lmmse_tcg16_kernel<256, G_FP16>, A, S);
+    if (e == cudaSuccess) e = set_tcg16_smem<G_BF16>(S);
+    if (e == cudaSuccess) e = set_tcg16_smem<G_FP16>(S);
     result[device] = e;
   });
   return result[device];
