@@ -433,27 +433,34 @@ template <int OP>
 __global__ void __launch_bounds__(256) tcg_stage_kernel(const float2* __restrict__ y, const float2* __restrict__ pil,
                                                         unsigned char* __restrict__ a_tiles, int R, int M, int N,
                                                         int B, int n_kc, int n_rt) {
-  constexpr int F4 = G16_KC / 4;                     // float4 (two subcarriers) per chunk row
+  // Thread -> one 16-byte core row (8 reals, 4 subcarriers) of a chunk row: loads of a warp
+  // cover 4 chunk rows x 128 contiguous bytes, stores fill whole 32-byte sectors.
+  constexpr int CC = G16_KC / 8;                     // core columns per chunk row
   const int c = blockIdx.x, rt = blockIdx.y, b = blockIdx.z;
   const int r0 = rt * G_ROWS, x0 = b * B + c * (G16_KC / 2);
   unsigned char* a = a_tiles + ((size_t(b) * n_rt + rt) * n_kc + c) * size_t(G16_A_PART);
-  const int c4 = threadIdx.x % F4;
+  const int cc = threadIdx.x % CC;
 #pragma unroll
-  for (int k = 0; k < G_ROWS * F4 / 256; ++k) {
-    const int row = int(threadIdx.x) / F4 + (256 / F4) * k, rg = r0 + row, sc = x0 + 2 * c4;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (rg < R && sc < N) {
-      const float4 yv = __ldg(reinterpret_cast<const float4*>(y + size_t(rg) * N + sc));
-      const float4 p = __ldg(reinterpret_cast<const float4*>(pil + size_t(rg / M) * N + sc));
-      const float i0 = __fdividef(1.0f, fmaf(p.x, p.x, p.y * p.y));
-      const float i1 = __fdividef(1.0f, fmaf(p.z, p.z, p.w * p.w));
-      v = make_float4(fmaf(yv.x, p.x, yv.y * p.y) * i0, fmaf(yv.y, p.x, -yv.x * p.y) * i0,
-                      fmaf(yv.z, p.z, yv.w * p.w) * i1, fmaf(yv.w, p.z, -yv.z * p.w) * i1);   // Eq. 9
+  for (int k = 0; k < G_ROWS * CC / 256; ++k) {
+    const int row = int(threadIdx.x) / CC + (256 / CC) * k, rg = r0 + row;
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {                    // two subcarriers per float4
+      const int sc = x0 + 4 * cc + 2 * h;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rg < R && sc < N) {
+        const float4 yv = __ldg(reinterpret_cast<const float4*>(y + size_t(rg) * N + sc));
+        const float4 p = __ldg(reinterpret_cast<const float4*>(pil + size_t(rg / M) * N + sc));
+        const float i0 = __fdividef(1.0f, fmaf(p.x, p.x, p.y * p.y));
+        const float i1 = __fdividef(1.0f, fmaf(p.z, p.z, p.w * p.w));
+        v = make_float4(fmaf(yv.x, p.x, yv.y * p.y) * i0, fmaf(yv.y, p.x, -yv.x * p.y) * i0,
+                        fmaf(yv.z, p.z, yv.w * p.w) * i1, fmaf(yv.w, p.z, -yv.z * p.w) * i1);   // Eq. 9
+      }
+      w[2 * h] = OP == G_FP16 ? pack_f16x2(v.x, v.y) : pack_bf16x2(v.x, v.y);
+      w[2 * h + 1] = OP == G_FP16 ? pack_f16x2(v.z, v.w) : pack_bf16x2(v.z, v.w);
     }
-    // four 16-bit reals: half of a 16-byte core row (eight reals)
-    const int off = (row >> 3) * int(G16_SBO) + (c4 >> 1) * 128 + (row & 7) * 16 + (c4 & 1) * 8;
-    *reinterpret_cast<uint2*>(a + off) = OP == G_FP16 ? make_uint2(pack_f16x2(v.x, v.y), pack_f16x2(v.z, v.w))
-                                                      : make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+    const int off = (row >> 3) * int(G16_SBO) + cc * 128 + (row & 7) * 16;
+    *reinterpret_cast<uint4*>(a + off) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
